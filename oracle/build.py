@@ -1,0 +1,31 @@
+"""Compile the C oracle (oracle/hgks_ref.c) into oracle/_build/libhgks_ref.so.
+
+Test infrastructure only.  Plain gcc, FP64, no FMA contraction (so x86 and Arm
+builds round identically apart from libm), OpenMP over interfaces only.
+"""
+import os
+import subprocess
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "hgks_ref.c")
+HDR = os.path.join(HERE, "hgks_ref.h")
+OUT_DIR = os.path.join(HERE, "_build")
+LIB = os.path.join(OUT_DIR, "libhgks_ref.so")
+
+
+def build_oracle(force=False):
+    """Build the oracle shared library if missing or stale; return its path."""
+    os.makedirs(OUT_DIR, exist_ok=True)
+    stale = force or not os.path.exists(LIB) or any(
+        os.path.getmtime(p) > os.path.getmtime(LIB) for p in (SRC, HDR))
+    if stale:
+        tmp = LIB + ".tmp.%d" % os.getpid()
+        cmd = ["gcc", "-std=c11", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
+               "-fPIC", "-shared", "-o", tmp, SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build_oracle(force=True))
