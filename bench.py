@@ -1,0 +1,291 @@
+"""Benchmark of the HGKS step on GB300: cell-updates/s on the Taylor-Green
+vortex 256^3 in FP64 (Ma 0.1, Re 1600, Pr 0.72, power-law viscosity,
+CFL 0.5), synthetic data (the exact-average TGV initial field).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--n 256]
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun, one process per GPU)
+every rank advances its own independent replica of the problem (the
+single-GPU method does not shard); value is the total over ranks and the
+time is the maximum over ranks.
+
+--impl reference times the CPU oracle (test infrastructure, the paper's
+method written out plainly in C) on this machine's host cores, on a bounded
+sample of the same workload: the same Taylor-Green vortex on a 32^3 grid,
+whose per-cell work equals that of the 256^3 grid.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+GAMMA = 1.4
+MA, RE, PR, OMEGA, CFL = 0.1, 1600.0, 0.72, 0.7, 0.5
+METRIC = "cell-updates/s TGV 256^3 FP64 vs mixed at stated error; serve p50/p99 ms"
+# Table 3 of the paper: 256^3 TGV, FP64, Tesla V100, 11.697 h for 20 t_c at dt = 8.925e-4
+PAPER_V100_CUPS = 256 ** 3 * (20.0 / 8.925e-4) / (11.697 * 3600.0)
+
+
+def tgv_kwargs():
+    p0 = 1.0 / (GAMMA * MA * MA)
+    return dict(visc=(1, 1.0 / RE, p0, OMEGA), Pr=PR, gamma=GAMMA)
+
+
+def workload_config(n):
+    import paper_2207_01173_gb300 as hg
+    fp = hg.footprint_bytes((n, n, n))
+    return {"workload": "Taylor-Green vortex %d^3 FP64, Ma %.1f, Re %d, Pr %.2f, power-law viscosity "
+                        "(omega %.1f), CFL %.1f" % (n, MA, RE, PR, OMEGA, CFL),
+            "grid": [n, n, n], "precision": "fp64",
+            "l2": "no flush: inputs larger than L2 (each state buffer %.0f MB, %.1f GB of device buffers per "
+                  "step against a 129 MB L2)" % (5 * (n + 6) ** 3 * 8 / 1e6, fp / 1e9),
+            "data": "synthetic exact-average TGV initial field"}
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# the oracle on the host cores (CPU baseline / reference arm)
+# --------------------------------------------------------------------------
+def oracle_rate(steps, n=32):
+    """cell-updates/s of the CPU oracle on the n^3 TGV (same per-cell work as
+    256^3), `steps` full steps after one untimed step."""
+    from oracle import ref
+    s = ref.RefSolver((n, n, n), **{k: v for k, v in tgv_kwargs().items()})
+    s.init_tgv(MA, 1.0, 1.0)
+    s.step(1, CFL)
+    t0 = time.perf_counter()
+    s.step(steps, CFL)
+    el = time.perf_counter() - t0
+    s.close()
+    return n ** 3 * steps / el, el
+
+
+def oracle_threads():
+    v = os.environ.get("OMP_NUM_THREADS")
+    return int(v) if v else os.cpu_count()
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    rate, el = oracle_rate(args.warmup, args.ref_n)  # warm-up steps (timed region below)
+    rate, el = oracle_rate(args.steps, args.ref_n)
+    cores = oracle_threads()
+    sample = "TGV %d^3 (same Ma, Re, Pr, viscosity law and CFL; per-cell work equals the %d^3 grid's), " \
+             "%d steps after 1 untimed" % (args.ref_n, args.n, args.steps)
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": "cell-updates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args.n),
+            "cpu_baseline": {"value": rate, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": rate, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------
+# the GPU path
+# --------------------------------------------------------------------------
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    # CPU baseline first (no GPU context yet), rank 0 only, N = 1 only
+    cpu_baseline = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, el = oracle_rate(args.cpu_steps, args.ref_n)
+        cpu_baseline = {"value": rate, "unit": "cell-updates/s", "cores": oracle_threads(), "kind": "oracle",
+                        "sample": "TGV %d^3, %d steps after 1 untimed (same per-cell work as %d^3), %.1f s"
+                                  % (args.ref_n, args.cpu_steps, args.n, el)}
+
+    torch.cuda.set_device(local_rank)
+    import paper_2207_01173_gb300 as hg
+
+    n = args.n
+    cells = n ** 3
+    solver = hg.Solver((n, n, n), **tgv_kwargs())
+    solver.init_tgv(MA, 1.0, 1.0)
+    stream = torch.cuda.current_stream()
+    model = hg.flop_model((n, n, n))
+    fp64_peak = hg.fp64_probe() if rank == 0 else None
+
+    for _ in range(args.warmup):
+        solver.step_timed(CFL)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    times = []
+    with ClockSampler(local_rank) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            times.append(solver.step_timed(CFL))
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = world * cells * args.steps / (ms * 1e-3)
+
+    # end to end through the public API with host buffers: pinned H2D of the
+    # state, one step, D2H of the resulting state, every step
+    q_host = torch.empty((5, n, n, n), dtype=torch.float64).pin_memory()
+    solver.get_state(q_host)
+    out_host = torch.empty_like(q_host).pin_memory()
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        solver.set_state(q_host)
+        solver.step(1, CFL)
+        solver.get_state(out_host)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * cells * e2e_steps / e2e_s
+    stats = solver.stats()
+
+    if rank != 0:
+        return 0
+    # dominant kernel: the flux pass (six launches per step)
+    flux_ms = sum(t["flux_ms"] for t in times)
+    flux_launches = sum(t["flux_launches"] for t in times)
+    launches = sum(t["launches"] for t in times)
+    kernel_ms = {k: sum(t[k] for t in times) / args.steps
+                 for k in ("ghost_ms", "dt_ms", "normal_ms", "tan1_ms", "flux_ms", "update_ms", "other_ms")}
+    faces_per_launch = (n + 1) * n * n
+    flops_per_launch = model["flux_per_face"] * faces_per_launch
+    achieved = flops_per_launch / (flux_ms / flux_launches * 1e-3) / 1e12
+    peak = 1.25  # nominal dense FP64, TFLOP/s
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": value / PAPER_V100_CUPS, "dtype": "f64", "data": "synthetic",
+        "config": dict(workload_config(n), parallelism=("replicas%d" % world) if world > 1 else "single-gpu"),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "k_flux",
+                     "peak_note": "nominal GB300 dense FP64 (1.25 TFLOP/s); measured FP64 FMA probe %.3f TFLOP/s"
+                                  % fp64_peak,
+                     "algorithmic_flops_per_launch": flops_per_launch,
+                     "flops_per_face": model["flux_per_face"], "faces_per_launch": faces_per_launch,
+                     "avg_launch_ms": flux_ms / flux_launches},
+        "step_flops": model["per_step"],
+        "step_tflops": model["per_step"] / (ms_per_step * 1e-3) / 1e12,
+        "kernel_ms_per_step": kernel_ms,
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "e2e": {"value": e2e_value, "unit": "cell-updates/s", "h2d_bytes_per_step": 5 * cells * 8,
+                "d2h_bytes_per_step": 5 * cells * 8, "steps": e2e_steps},
+        "cpu_baseline": cpu_baseline,
+        "final_stats": {"t": stats["t"], "step": stats["step"], "Ek": stats["Ek"], "enstrophy": stats["enstrophy"]},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--ref-n", type=int, default=32)
+    ap.add_argument("--cpu-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("at least 3 warm-up steps")
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world != args.gpus:
+        world = max(world, 1)
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    try:
+        return run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

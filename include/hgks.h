@@ -1,0 +1,207 @@
+/*
+ * hgks.h -- C-ABI of the GB300 (sm_103a) high-order gas-kinetic scheme (HGKS)
+ * library, libhgks.so.
+ *
+ * The method is that of "Multiple-GPU accelerated high-order gas-kinetic
+ * scheme for direct numerical simulation of compressible turbulence"
+ * (arXiv 2207.01173), Sec. 2: the finite-volume semi-discretisation
+ * dQ/dt = L(Q) (Eqs. "semi", "semi2") on a structured hexahedral grid, the
+ * BGK gas-kinetic interface flux at the 2x2 Gauss points of every face
+ * (Eq. "flux" and the compatibility / micro-slope conditions that follow it),
+ * its linear-in-time fit (Eq. "expansion-1") and the two-stage fourth-order
+ * time update (Eq. "two-stage"), with fifth-order WENO reconstruction applied
+ * dimension by dimension.  The test problems are the Taylor-Green vortex
+ * (Sec. 4.1) and the compressible channel flow (Sec. 4.2).
+ *
+ * Conventions
+ *   - Every entry point returns an hgks_status; results go through
+ *     out-pointers.  HGKS_OK is 0.
+ *   - The library owns all device memory of a handle (allocated at
+ *     hgks_create, freed at hgks_destroy).
+ *   - Host buffers passed in are owned by the caller; the library copies
+ *     them and never keeps a pointer.  Calls that read or write host
+ *     buffers return only after the copy has completed.
+ *   - Work is enqueued on the CUDA stream given at hgks_create (NULL = the
+ *     legacy default stream).  hgks_step is asynchronous except for one
+ *     status read at its end.
+ *   - A handle is used by one host thread at a time.
+ *   - Conservative state layout for host buffers: double[5][nz][ny][nx],
+ *     components (rho, rho U, rho V, rho W, rho E), x fastest.
+ *   - Units: gas constant R = 1, so p = rho T and lambda = rho / (2 p).
+ *   - The product path never falls back to the CPU: if no usable CUDA
+ *     device is present hgks_create fails with HGKS_ERR_CUDA.
+ */
+#ifndef HGKS_H
+#define HGKS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hgks_s *hgks_t; /* opaque handle */
+
+typedef enum {
+    HGKS_OK = 0,
+    HGKS_ERR_INVALID_ARG = 1, /* a NULL pointer, a size or parameter out of range */
+    HGKS_ERR_OOM = 2,         /* device allocation failed */
+    HGKS_ERR_CUDA = 3,        /* a CUDA runtime call failed (see hgks_last_error) */
+    HGKS_ERR_NONFINITE = 4,   /* a step produced a non-finite value or rho <= 0 or p <= 0;
+                                 the state is left at the last completed step */
+    HGKS_ERR_TIMEOUT = 5,     /* reserved for bounded device-side waits */
+    HGKS_ERR_STATE = 6        /* call not valid in the handle's current state */
+} hgks_status;
+
+typedef enum { HGKS_BC_PERIODIC = 0, HGKS_BC_ISOTHERMAL_WALL = 1 } hgks_bc;
+typedef enum { HGKS_VISC_CONSTANT = 0, HGKS_VISC_POWER = 1 } hgks_visc_kind;
+typedef enum { HGKS_FP64 = 0, HGKS_MIXED = 1 } hgks_precision;
+
+/* Structured grid (Sec. 2 "orthogonal structured mesh"; Sec. 4.2 mesh map).
+ * nx, ny, nz >= 1 cells.  Uniform spacing lx/nx and lz/nz in x and z.
+ * y_stretch_b = 0: uniform y; y_stretch_b = b > 0: y faces at
+ *   y_j = y0 + ly/2 (1 + tanh(b (2j/ny - 1)) / tanh(b)), j = 0..ny,
+ * which for y0 = -1, ly = 2 is the channel map of Sec. 4.2. */
+typedef struct {
+    int nx, ny, nz;
+    double lx, ly, lz;
+    double x0, y0, z0;
+    double y_stretch_b;
+} hgks_grid;
+
+/* Viscosity law (Sec. 4.2): mu = mu_ref (T / T_ref)^omega for POWER,
+ * mu = mu_ref for CONSTANT.  The collision time is tau = mu / p (Sec. 2). */
+typedef struct {
+    hgks_visc_kind kind;
+    double mu_ref, T_ref, omega;
+} hgks_visc;
+
+/* Boundary conditions per direction and side (Sec. 4: periodic in every
+ * direction for the TGV; periodic x, z and no-slip isothermal walls in y for
+ * the channel).  Walls need at least 3 cells in their direction. */
+typedef struct {
+    hgks_bc lo[3], hi[3];
+    double T_wall;
+} hgks_bcs;
+
+/* Diagnostics (Sec. 4.1 definitions of E_k and eps_com). */
+typedef struct {
+    double t;          /* simulated time */
+    int64_t step;      /* completed steps */
+    double dt;         /* time step of the last completed step */
+    double Ek;         /* (1 / (rho0 Omega)) sum 1/2 rho |u|^2 |Omega_i| */
+    double enstrophy;  /* (1 / (rho0 Omega)) sum 1/2 rho |omega|^2 |Omega_i| */
+    double eps_com;    /* (1 / (rho0 Omega)) sum mu (|omega|^2 + 4/3 (div u)^2) |Omega_i| */
+    double mass, mom[3], energy; /* sums of Q |Omega_i| */
+    double max_mach;   /* max |u| / c over cells */
+    double wall_shear; /* mean x-momentum wall flux per unit wall area of the last step's
+                          first stage (walls only, else 0) */
+} hgks_stats_t;
+
+/* Create a solver.
+ *   grid, visc, bcs: see above (copied).  gamma > 1 (internal degrees of
+ *   freedom K = (5 - 3 gamma)/(gamma - 1), Sec. 2).  Pr > 0 (Prandtl number,
+ *   applied to the energy flux as F_E += (1/Pr - 1) q).
+ *   body_force: constant acceleration (G_x, G_y, G_z) or NULL for none.
+ *   precision: HGKS_FP64 (all arithmetic FP64) or HGKS_MIXED (FP32
+ *   reconstruction and flux arithmetic, FP64 state, collision time and
+ *   equilibrium; HGKS_ERR_INVALID_ARG until that path is built).
+ *   cuda_stream: a cudaStream_t, or NULL.
+ *   out: receives the handle.
+ * Errors: INVALID_ARG, OOM, CUDA (no device / context failure). */
+hgks_status hgks_create(const hgks_grid *grid, double gamma, double Pr, const hgks_visc *visc,
+                        const hgks_bcs *bcs, const double body_force[3], hgks_precision precision,
+                        void *cuda_stream, hgks_t *out);
+
+/* Taylor-Green vortex of Sec. 4.1 on the grid's box as exact cell averages:
+ * u = U0 sin x cos y cos z, v = -U0 cos x sin y cos z, w = 0, rho = rho0,
+ * p = p0 + rho0 U0^2/16 (cos 2x + cos 2y)(cos 2z + 2), p0 = rho0 U0^2/(gamma Ma^2).
+ * Resets t and step to 0.  Sets the stats reference density to rho0. */
+hgks_status hgks_init_tgv(hgks_t h, double Ma, double U0, double rho0);
+
+/* Perturbed Poiseuille channel of Sec. 4.2 (point values at cell centres):
+ * rho = 1, T = T_w = 1/(gamma Ma_b^2) (U_b = 1), U = 1.5 (1 - yn^2) with yn the
+ * wall-normal coordinate scaled to [-1, 1]; u = U (1 + a r0), v = a r1, w = a r2,
+ * a = noise_amp, r_c uniform in [-1, 1) from splitmix64(seed ^ (3 idx + c)),
+ * idx = (k ny + j) nx + i.  Sets the wall temperature to T_w. */
+hgks_status hgks_init_channel(hgks_t h, double Ma_b, double noise_amp, uint64_t seed);
+
+/* Smooth density wave for convergence studies: exact cell averages of
+ * rho = 1 + amp sin(pi sum_d k_d x_d), U_d = k_d, p = 1, with k_d = 1 for every
+ * direction that has more than one cell and 0 otherwise. */
+hgks_status hgks_init_density_wave(hgks_t h, double amp);
+
+/* Copy a host state double[5][nz][ny][nx] in / out (blocking). */
+hgks_status hgks_set_state(hgks_t h, const double *host_q);
+hgks_status hgks_get_state(hgks_t h, double *host_q);
+/* Set the simulated time and step counter (e.g. when resuming). */
+hgks_status hgks_set_time(hgks_t h, double t, int64_t step);
+
+/* Advance nsteps S2O4 steps.  Each step fills the ghost cells, takes
+ * dt = cfl * min over cells and directions of dx_d / (|u_d| + c) (Alg. 1 STEP 1)
+ * and runs the two stages of Eq. "two-stage" with that dt.
+ * Errors: INVALID_ARG (nsteps < 0, cfl <= 0), NONFINITE, CUDA. */
+hgks_status hgks_step(hgks_t h, int nsteps, double cfl);
+/* As hgks_step with a fixed time step dt > 0. */
+hgks_status hgks_step_dt(hgks_t h, int nsteps, double dt);
+/* The CFL time step of the current state (blocking). */
+hgks_status hgks_compute_dt(hgks_t h, double cfl, double *dt);
+
+/* L(Q) and dL/dt(Q) of the current state (Eq. "semi2" and its time
+ * derivative, F^n and dF^n/dt from the fit over dt and dt/2), as host
+ * arrays double[5][nz][ny][nx].  For testing the flux path in isolation. */
+hgks_status hgks_rhs(hgks_t h, double dt, double *host_L, double *host_dL);
+
+/* Device time of one step split by kernel kind (CUDA events recorded on the
+ * handle's stream between the launches). */
+typedef struct {
+    double total_ms;                 /* first to last launch of the step */
+    double ghost_ms, dt_ms;          /* ghost fill (2 per step), CFL reduction */
+    double normal_ms, tan1_ms, flux_ms; /* the three sweep passes, summed over 2 stages x 3 sweeps */
+    double update_ms, other_ms;      /* stage updates; wall stress and commit */
+    int launches;                    /* kernels launched in the step */
+    int flux_launches;               /* launches of the flux pass */
+} hgks_step_times_t;
+/* One step as hgks_step(h, 1, cfl) with the per-kind device times. */
+hgks_status hgks_step_timed(hgks_t h, double cfl, hgks_step_times_t *out);
+
+/* Measured FP64 fused-multiply-add throughput of the current device in
+ * TFLOP/s (2 flops per FMA), from a short dependent-chain kernel. */
+hgks_status hgks_fp64_probe(double *tflops);
+
+/* Diagnostics of the current state (blocking). */
+hgks_status hgks_stats(hgks_t h, hgks_stats_t *out);
+
+/* Algorithmic floating-point work of the step, from the kernels' own
+ * arithmetic run on the host with an operation-counting scalar type.
+ * +, -, * count 1 (a fused multiply-add 2); division, sqrt, exp, erfc and pow
+ * count 1 each and are also given on their own for the flux pass.  Index
+ * arithmetic and comparisons count 0.  Host only; needs no device. */
+typedef struct {
+    double normal_per_face;       /* normal reconstruction, per position of its pass */
+    double tan1_per_pos;          /* first tangential reconstruction, per position */
+    double flux_per_face;         /* second tangential reconstruction + 4 Gauss-point fluxes, per face */
+    double div_per_face_flux;     /* divisions inside flux_per_face */
+    double special_per_face_flux; /* sqrt / exp / erfc / pow inside flux_per_face */
+    double per_step;              /* all passes of one two-stage step on the grid */
+} hgks_flop_model_t;
+hgks_status hgks_flop_model(const hgks_grid *grid, hgks_precision precision, hgks_flop_model_t *out);
+
+/* Device bytes a handle for this grid and precision allocates (admission). */
+size_t hgks_footprint_bytes(const hgks_grid *grid, hgks_precision precision);
+
+/* Message of the last error on this handle (or a global message for
+ * h == NULL).  Valid until the next call on the handle. */
+const char *hgks_last_error(hgks_t h);
+
+/* Wait for all work of the handle's stream. */
+hgks_status hgks_synchronize(hgks_t h);
+
+/* Release the handle and its device memory.  NULL is ignored. */
+void hgks_destroy(hgks_t h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HGKS_H */

@@ -719,6 +719,84 @@ static void normal_recon(const hgks_ref_t h, const double *q, int d, int f, int 
     compat_g(&gl, &gr, out[FQ_Q0]);
 }
 
+/* flux of one face (f, a, b) of sweep d from the normal-reconstruction records
+   of its 5x5 tangential neighbourhood: rec[jj][kk] is the record at tangential
+   offsets (jj - 2, kk - 2).  Returns F^n and dF^n/dt times the face area, in
+   the global component order. */
+static void face_flux_one(const hgks_ref_t h, int d, int f, int a, int b, double dt, const double *rec[5][5],
+                          double Fout[5], double dFout[5])
+{
+    const weno_point *gpt[2] = { &wp[WP_GM], &wp[WP_GP] };
+    static const int wq[5] = { FQ_QL, FQ_QR, FQ_DQL, FQ_DQR, FQ_DQ0 }; /* WENO-Z tangentially */
+    static const int lq[3] = { FQ_QL, FQ_QR, FQ_Q0 };                  /* linear value/derivative */
+    double Fsum[5] = { 0, 0, 0, 0, 0 }, dFsum[5] = { 0, 0, 0, 0, 0 };
+    int ijk[3];
+    cell_ijk(d, f, a, b, ijk);
+    double area;
+    if (d == 0) area = dy_cell(h, ijk[1]) * dz_(h);
+    else if (d == 1) area = dx_(h) * dz_(h);
+    else area = dx_(h) * dy_cell(h, ijk[1]);
+    double hn = metric(h, d, (double)f);
+    for (int m = 0; m < 2; m++) {
+        double T1V[5][5][5], T1L[5][3][5], T1D[5][3][5]; /* [t2 row][quantity][comp] */
+        for (int kk = 0; kk < 5; kk++) {
+            for (int c = 0; c < 5; c++) {
+                double X[5];
+                for (int qi = 0; qi < 5; qi++) {
+                    for (int jj = 0; jj < 5; jj++) X[jj] = rec[jj][kk][wq[qi] * 5 + c];
+                    T1V[kk][qi][c] = weno_z_at(X, gpt[m]);
+                }
+                for (int qi = 0; qi < 3; qi++) {
+                    for (int jj = 0; jj < 5; jj++) X[jj] = rec[jj][kk][lq[qi] * 5 + c];
+                    T1L[kk][qi][c] = dot5(gpt[m]->qv, X);
+                    T1D[kk][qi][c] = dot5(gpt[m]->qd, X);
+                }
+            }
+        }
+        double h1 = metric(h, tdir[d][0], a + 0.5 + gpt[m]->sigma);
+        for (int n = 0; n < 2; n++) {
+            double h2 = metric(h, tdir[d][1], b + 0.5 + gpt[n]->sigma);
+            double V[5][5], Dt1[3][5], Dt2[3][5];
+            for (int c = 0; c < 5; c++) {
+                double X[5];
+                for (int qi = 0; qi < 5; qi++) {
+                    for (int kk = 0; kk < 5; kk++) X[kk] = T1V[kk][qi][c];
+                    V[qi][c] = weno_z_at(X, gpt[n]);
+                }
+                for (int qi = 0; qi < 3; qi++) {
+                    for (int kk = 0; kk < 5; kk++) X[kk] = T1D[kk][qi][c];
+                    Dt1[qi][c] = dot5(gpt[n]->qv, X);
+                    for (int kk = 0; kk < 5; kk++) X[kk] = T1L[kk][qi][c];
+                    Dt2[qi][c] = dot5(gpt[n]->qd, X);
+                }
+            }
+            double dQl[3][5], dQr[3][5], dQ0[3][5];
+            for (int c = 0; c < 5; c++) {
+                dQl[0][c] = V[2][c] / hn;
+                dQr[0][c] = V[3][c] / hn;
+                dQ0[0][c] = V[4][c] / hn;
+                dQl[1][c] = Dt1[0][c] / h1;
+                dQr[1][c] = Dt1[1][c] / h1;
+                dQ0[1][c] = Dt1[2][c] / h1;
+                dQl[2][c] = Dt2[0][c] / h2;
+                dQr[2][c] = Dt2[1][c] / h2;
+                dQ0[2][c] = Dt2[2][c] / h2;
+            }
+            double If[5], Ih[5], Fn[5], dFn[5];
+            point_flux(&h->gas, V[0], V[1], dQl, dQr, dQ0, dt, If, Ih);
+            hgks_ref_time_fit(If, Ih, dt, Fn, dFn);
+            for (int c = 0; c < 5; c++) {
+                Fsum[c] += 0.25 * Fn[c];
+                dFsum[c] += 0.25 * dFn[c];
+            }
+        }
+    }
+    for (int c = 0; c < 5; c++) {
+        Fout[perm[d][c]] = Fsum[c] * area;
+        dFout[perm[d][c]] = dFsum[c] * area;
+    }
+}
+
 static void face_fluxes(const hgks_ref_t h, const double *q, int d, double dt, double *Fo, double *dFo)
 {
     const int nd = n_of(h, d), n1 = n_of(h, tdir[d][0]), n2 = n_of(h, tdir[d][1]);
@@ -738,90 +816,40 @@ static void face_fluxes(const hgks_ref_t h, const double *q, int d, double dt, d
     }
 
     /* 2. tangential reconstruction to the 2x2 Gauss points and the GKS flux */
-    const weno_point *gpt[2] = { &wp[WP_GM], &wp[WP_GP] };
-    static const int wq[5] = { FQ_QL, FQ_QR, FQ_DQL, FQ_DQR, FQ_DQ0 }; /* WENO-Z tangentially */
-    static const int lq[3] = { FQ_QL, FQ_QR, FQ_Q0 };                  /* linear value/derivative */
 #pragma omp parallel for schedule(dynamic, 16)
     for (long fidx = 0; fidx < (long)nface; fidx++) {
         int f = (int)(fidx % (nd + 1));
         int a = (int)((fidx / (nd + 1)) % n1);
         int b = (int)(fidx / ((long)(nd + 1) * n1));
-        double Fsum[5] = { 0, 0, 0, 0, 0 }, dFsum[5] = { 0, 0, 0, 0, 0 };
-        /* face area and metrics */
-        int ijk[3];
-        cell_ijk(d, f, a, b, ijk);
-        double area;
-        if (d == 0) area = dy_cell(h, ijk[1]) * dz_(h);
-        else if (d == 1) area = dx_(h) * dz_(h);
-        else area = dx_(h) * dy_cell(h, ijk[1]);
-        double hn = metric(h, d, (double)f);
-        for (int m = 0; m < 2; m++) {
-            double T1V[5][5][5], T1L[5][3][5], T1D[5][3][5]; /* [t2 row][quantity][comp] */
+        const double *rec[5][5];
+        for (int jj = 0; jj < 5; jj++)
             for (int kk = 0; kk < 5; kk++) {
-                const double *base[5];
-                for (int jj = 0; jj < 5; jj++) {
-                    size_t fi = ((size_t)(b + kk) * e1 + (size_t)(a + jj)) * (nd + 1) + f; /* rows b-2+kk, a-2+jj (shifted) */
-                    base[jj] = &FQ[fi * FQ_N * 5];
-                }
-                for (int c = 0; c < 5; c++) {
-                    double X[5];
-                    for (int qi = 0; qi < 5; qi++) {
-                        for (int jj = 0; jj < 5; jj++) X[jj] = base[jj][wq[qi] * 5 + c];
-                        T1V[kk][qi][c] = weno_z_at(X, gpt[m]);
-                    }
-                    for (int qi = 0; qi < 3; qi++) {
-                        for (int jj = 0; jj < 5; jj++) X[jj] = base[jj][lq[qi] * 5 + c];
-                        T1L[kk][qi][c] = dot5(gpt[m]->qv, X);
-                        T1D[kk][qi][c] = dot5(gpt[m]->qd, X);
-                    }
-                }
+                size_t fi = ((size_t)(b + kk) * e1 + (size_t)(a + jj)) * (nd + 1) + f; /* offsets -2..2, shifted */
+                rec[jj][kk] = &FQ[fi * FQ_N * 5];
             }
-            double h1 = metric(h, tdir[d][0], a + 0.5 + gpt[m]->sigma);
-            for (int n = 0; n < 2; n++) {
-                double h2 = metric(h, tdir[d][1], b + 0.5 + gpt[n]->sigma);
-                double V[5][5], Dt1[3][5], Dt2[3][5];
-                for (int c = 0; c < 5; c++) {
-                    double X[5];
-                    for (int qi = 0; qi < 5; qi++) {
-                        for (int kk = 0; kk < 5; kk++) X[kk] = T1V[kk][qi][c];
-                        V[qi][c] = weno_z_at(X, gpt[n]);
-                    }
-                    for (int qi = 0; qi < 3; qi++) {
-                        for (int kk = 0; kk < 5; kk++) X[kk] = T1D[kk][qi][c];
-                        Dt1[qi][c] = dot5(gpt[n]->qv, X);
-                        for (int kk = 0; kk < 5; kk++) X[kk] = T1L[kk][qi][c];
-                        Dt2[qi][c] = dot5(gpt[n]->qd, X);
-                    }
-                }
-                double dQl[3][5], dQr[3][5], dQ0[3][5];
-                for (int c = 0; c < 5; c++) {
-                    dQl[0][c] = V[2][c] / hn;
-                    dQr[0][c] = V[3][c] / hn;
-                    dQ0[0][c] = V[4][c] / hn;
-                    dQl[1][c] = Dt1[0][c] / h1;
-                    dQr[1][c] = Dt1[1][c] / h1;
-                    dQ0[1][c] = Dt1[2][c] / h1;
-                    dQl[2][c] = Dt2[0][c] / h2;
-                    dQr[2][c] = Dt2[1][c] / h2;
-                    dQ0[2][c] = Dt2[2][c] / h2;
-                }
-                double If[5], Ih[5], Fn[5], dFn[5];
-                point_flux(&h->gas, V[0], V[1], dQl, dQr, dQ0, dt, If, Ih);
-                hgks_ref_time_fit(If, Ih, dt, Fn, dFn);
-                for (int c = 0; c < 5; c++) {
-                    Fsum[c] += 0.25 * Fn[c];
-                    dFsum[c] += 0.25 * dFn[c];
-                }
-            }
-        }
-        /* back to global component order, scaled by the face area */
-        size_t fo = fidx; /* face order (f fastest, then a, then b) */
+        double Fl[5], dFl[5];
+        face_flux_one(h, d, f, a, b, dt, rec, Fl, dFl);
         for (int c = 0; c < 5; c++) {
-            Fo[(size_t)perm[d][c] * nface + fo] = Fsum[c] * area;
-            dFo[(size_t)perm[d][c] * nface + fo] = dFsum[c] * area;
+            Fo[(size_t)c * nface + fidx] = Fl[c];
+            dFo[(size_t)c * nface + fidx] = dFl[c];
         }
     }
     free(FQ);
+}
+
+/* the same face flux with the 25 neighbouring normal reconstructions done on
+   the spot (for sampled interfaces of large grids) */
+static void face_flux_local(const hgks_ref_t h, const double *q, int d, int f, int a, int b, double dt,
+                            double Fl[5], double dFl[5])
+{
+    double recs[5][5][FQ_N * 5];
+    const double *rec[5][5];
+    for (int jj = 0; jj < 5; jj++)
+        for (int kk = 0; kk < 5; kk++) {
+            normal_recon(h, q, d, f, a - 2 + jj, b - 2 + kk, (double(*)[5])recs[jj][kk]);
+            rec[jj][kk] = recs[jj][kk];
+        }
+    face_flux_one(h, d, f, a, b, dt, rec, Fl, dFl);
 }
 
 /* L(Q) and dL/dt(Q) (Eq. "semi2" and its time derivative) of a ghost-filled state */
@@ -1131,6 +1159,44 @@ int hgks_ref_rhs(hgks_ref_t h, double dt, double *L, double *dL)
     if (st) return fail(h, st, "out of memory");
     ghost_fill(h, h->q);
     eval_rhs(h, h->q, dt, L, dL, 0);
+    return HGKS_REF_OK;
+}
+
+/* L and dL/dt at a list of interior cells only (cell index (k ny + j) nx + i) */
+int hgks_ref_rhs_cells(hgks_ref_t h, double dt, int ncells, const int64_t *cells, double *L, double *dL)
+{
+    if (!h || !cells || !L || !dL || ncells < 0 || !(dt > 0.0)) return HGKS_REF_ERR_INVALID_ARG;
+    ghost_fill(h, h->q);
+    const int nx = h->g.nx, ny = h->g.ny;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int s = 0; s < ncells; s++) {
+        int64_t ci = cells[s];
+        int i = (int)(ci % nx), j = (int)((ci / nx) % ny), k = (int)(ci / ((int64_t)nx * ny));
+        int ijk[3] = { i, j, k };
+        double sd[3][5], tdd[3][5];
+        for (int d = 0; d < 3; d++) {
+            int f = ijk[d], a = ijk[tdir[d][0]], b = ijk[tdir[d][1]];
+            double Fm[5], dFm[5], Fp[5], dFp[5];
+            face_flux_local(h, h->q, d, f, a, b, dt, Fm, dFm);
+            face_flux_local(h, h->q, d, f + 1, a, b, dt, Fp, dFp);
+            for (int c = 0; c < 5; c++) { sd[d][c] = Fp[c] - Fm[c]; tdd[d][c] = dFp[c] - dFm[c]; }
+        }
+        double vol = dx_(h) * dy_cell(h, j) * dz_(h);
+        double Lc[5], dLc[5];
+        for (int c = 0; c < 5; c++) {
+            Lc[c] = -((sd[0][c] + sd[1][c]) + sd[2][c]) / vol;
+            dLc[c] = -((tdd[0][c] + tdd[1][c]) + tdd[2][c]) / vol;
+        }
+        if (h->G[0] != 0.0 || h->G[1] != 0.0 || h->G[2] != 0.0) {
+            size_t p = pidx(h, i, j, k), S = h->ncell_pad;
+            double rho = h->q[p];
+            for (int e = 0; e < 3; e++) Lc[1 + e] += rho * h->G[e];
+            Lc[4] += h->q[1 * S + p] * h->G[0] + h->q[2 * S + p] * h->G[1] + h->q[3 * S + p] * h->G[2];
+            for (int e = 0; e < 3; e++) dLc[1 + e] += h->G[e] * Lc[0];
+            dLc[4] += h->G[0] * Lc[1] + h->G[1] * Lc[2] + h->G[2] * Lc[3];
+        }
+        for (int c = 0; c < 5; c++) { L[(size_t)s * 5 + c] = Lc[c]; dL[(size_t)s * 5 + c] = dLc[c]; }
+    }
     return HGKS_REF_OK;
 }
 

@@ -52,6 +52,8 @@ int  hgks_ref_step(hgks_ref_t h, int nsteps, double cfl);
 int  hgks_ref_step_dt(hgks_ref_t h, int nsteps, double dt);
 int  hgks_ref_compute_dt(hgks_ref_t h, double cfl, double *dt);
 int  hgks_ref_rhs(hgks_ref_t h, double dt, double *L, double *dL); /* L(Q), dL/dt(Q) of current state */
+/* L, dL/dt at sampled interior cells (index (k ny + j) nx + i); outputs [ncells][5] */
+int  hgks_ref_rhs_cells(hgks_ref_t h, double dt, int ncells, const int64_t *cells, double *L, double *dL);
 int  hgks_ref_stats(hgks_ref_t h, hgks_ref_stats_t *out);
 const char *hgks_ref_last_error(hgks_ref_t h);
 void hgks_ref_destroy(hgks_ref_t h);

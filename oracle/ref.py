@@ -62,6 +62,7 @@ def lib():
         L.hgks_ref_step_dt.argtypes = [C.c_void_p, C.c_int, C.c_double]
         L.hgks_ref_compute_dt.argtypes = [C.c_void_p, C.c_double, _D]
         L.hgks_ref_rhs.argtypes = [C.c_void_p, C.c_double, _D, _D]
+        L.hgks_ref_rhs_cells.argtypes = [C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_int64), _D, _D]
         L.hgks_ref_stats.argtypes = [C.c_void_p, C.POINTER(Stats)]
         L.hgks_ref_last_error.argtypes = [C.c_void_p]
         L.hgks_ref_last_error.restype = C.c_char_p
@@ -186,6 +187,15 @@ class RefSolver:
         L = np.empty(self.shape)
         dL = np.empty(self.shape)
         self._check(lib().hgks_ref_rhs(self.h, dt, _p(L), _p(dL)), "rhs")
+        return L, dL
+
+    def rhs_cells(self, dt, cells):
+        """L, dL at interior cells given by linear index (k ny + j) nx + i; returns [n][5] arrays."""
+        idx = np.ascontiguousarray(np.asarray(cells, dtype=np.int64))
+        L = np.empty((idx.size, 5))
+        dL = np.empty((idx.size, 5))
+        self._check(lib().hgks_ref_rhs_cells(self.h, dt, idx.size, idx.ctypes.data_as(C.POINTER(C.c_int64)),
+                                             _p(L), _p(dL)), "rhs_cells")
         return L, dL
 
     def stats(self):

@@ -1,0 +1,171 @@
+// hgks_bodies.cuh -- the arithmetic of one interface position of each sweep
+// pass, as templates on the scalar type and on load/store functors.  The CUDA
+// kernels instantiate them with double and global-memory accessors; the host
+// flop model instantiates the same bodies with an operation-counting type.
+#pragma once
+#include "hgks_device.cuh"
+
+namespace hgks {
+
+// normal reconstruction of one face (arXiv 2207.01173 Sec. 2, WENO of the cell
+// averages along the face normal).  load(c, m): rotated component c of the
+// m-th cell of the six along the normal (cells f-3 .. f+2).  Stores 30 slots:
+// 0-4 Ql, 5-9 Qr, 10-14 dQl, 15-19 dQr, 20-24 Q0 (compatibility), 25-29 dQ0,
+// slopes in index units.
+template <typename T, typename Load, typename Store>
+HGKS_HD void normal_body(Load load, Store store, double K)
+{
+    T Ql[5], Qr[5];
+#pragma unroll
+    for (int c = 0; c < 5; c++) {
+        T X[6];
+#pragma unroll
+        for (int m = 0; m < 6; m++) X[m] = load(c, m);
+        WenoPrep<T> wl, wr;
+        weno_prep(X, wl);      // cell f-1
+        weno_prep(X + 1, wr);  // cell f
+        T lm_r = weno_edge(wl, 1), lm_l = weno_edge(wl, 0);
+        T r_l = weno_edge(wr, 0), r_r = weno_edge(wr, 1);
+        Ql[c] = lm_r;
+        Qr[c] = r_l;
+        store(0 * 5 + c, lm_r);
+        store(1 * 5 + c, r_l);
+        // parabola through (left edge, average, right edge) of a cell, slope at its ends
+        store(2 * 5 + c, 2.0 * lm_l + 4.0 * lm_r - 6.0 * X[2]);
+        store(3 * 5 + c, -4.0 * r_l - 2.0 * r_r + 6.0 * X[3]);
+        // cubic through four averages, slope at the face
+        store(5 * 5 + c, (15.0 * (X[3] - X[2]) - (X[4] - X[1])) * (1.0 / 12.0));
+    }
+    // face-averaged equilibrium from the compatibility condition
+    Prim<T> gl = prim_of(Ql, K), gr = prim_of(Qr, K);
+    T il = 0.5 / gl.lam, ir = 0.5 / gr.lam;
+    T ulp[3], vl[3], wl[3], urn[3], vr[3], wr[3];
+    mom_half<3>(gl.U, gl.lam, il, true, ulp);
+    mom_full<3>(gl.V, il, vl);
+    mom_full<3>(gl.W, il, wl);
+    mom_half<3>(gr.U, gr.lam, ir, false, urn);
+    mom_full<3>(gr.V, ir, vr);
+    mom_full<3>(gr.W, ir, wr);
+    Mom<T> Ml{ ulp, vl, wl, K * il, T(0.0) }, Mr{ urn, vr, wr, K * ir, T(0.0) };
+    T a[5], b[5];
+    psi_mom<0, 0, 0>(Ml, a);
+    psi_mom<0, 0, 0>(Mr, b);
+#pragma unroll
+    for (int c = 0; c < 5; c++) store(4 * 5 + c, gl.rho * a[c] + gr.rho * b[c]);
+}
+
+// first tangential direction of one face row.  load(slot, j): normal-pass slot
+// at tangential offset j - 2.  Stores 110 slots: for Gauss line m (0, 1) at
+// m*55: 25 WENO-Z values (Ql, Qr, dQl, dQr, dQ0), 15 quartic values and 15
+// quartic derivatives (Ql, Qr, Q0).
+template <typename T, typename Load, typename Store>
+HGKS_HD void tan1_body(Load load, Store store)
+{
+#pragma unroll 1
+    for (int w = 0; w < 5; w++) {
+        const int slot = w < 4 ? w : 5;
+#pragma unroll
+        for (int c = 0; c < 5; c++) {
+            T X[5];
+#pragma unroll
+            for (int j = 0; j < 5; j++) X[j] = load(slot * 5 + c, j);
+            WenoPrep<T> W;
+            weno_prep(X, W);
+            store(0 * 55 + w * 5 + c, weno_gauss(W, 0));
+            store(1 * 55 + w * 5 + c, weno_gauss(W, 1));
+        }
+    }
+#pragma unroll 1
+    for (int l = 0; l < 3; l++) {
+        const int slot = l < 2 ? l : 4;
+#pragma unroll
+        for (int c = 0; c < 5; c++) {
+            T X[5];
+#pragma unroll
+            for (int j = 0; j < 5; j++) X[j] = load(slot * 5 + c, j);
+#pragma unroll
+            for (int m = 0; m < 2; m++) {
+                store(m * 55 + 25 + l * 5 + c, quartic_value(X, m));
+                store(m * 55 + 40 + l * 5 + c, quartic_deriv(X, m));
+            }
+        }
+    }
+}
+
+// geometry of one face: normal metric, tangential metrics at the Gauss
+// abscissae, area
+struct FaceGeom {
+    double hn, h1[2], h2[2], area;
+};
+
+// second tangential direction, the four Gauss-point fluxes and their sum.
+// load(slot, j): first-pass slot at offset j - 2 along the second tangential
+// direction.  Fs, dFs: F^n and dF^n/dt times the face area, rotated frame.
+template <typename T, typename Load>
+HGKS_HD void flux_body(Load load, const FaceGeom &G, const Params &P, T dt, T Fs[5], T dFs[5])
+{
+#pragma unroll
+    for (int c = 0; c < 5; c++) {
+        Fs[c] = T(0.0);
+        dFs[c] = T(0.0);
+    }
+#pragma unroll 1
+    for (int m = 0; m < 2; m++) {
+        const double h1 = G.h1[m];
+        T gv[2][25], gd1[2][15], gd2[2][15];
+#pragma unroll 1
+        for (int k = 0; k < 25; k++) {
+            T X[5];
+#pragma unroll
+            for (int j = 0; j < 5; j++) X[j] = load(m * 55 + k, j);
+            WenoPrep<T> W;
+            weno_prep(X, W);
+            gv[0][k] = weno_gauss(W, 0);
+            gv[1][k] = weno_gauss(W, 1);
+        }
+#pragma unroll 1
+        for (int k = 0; k < 15; k++) {
+            T X[5], Y[5];
+#pragma unroll
+            for (int j = 0; j < 5; j++) {
+                X[j] = load(m * 55 + 40 + k, j);  // first-direction derivatives
+                Y[j] = load(m * 55 + 25 + k, j);  // first-direction quartic values
+            }
+            gd1[0][k] = quartic_value(X, 0);
+            gd1[1][k] = quartic_value(X, 1);
+            gd2[0][k] = quartic_deriv(Y, 0);
+            gd2[1][k] = quartic_deriv(Y, 1);
+        }
+#pragma unroll 1
+        for (int n = 0; n < 2; n++) {
+            const double h2 = G.h2[n];
+            T dl[3][5], dr[3][5], d0[3][5];
+#pragma unroll
+            for (int c = 0; c < 5; c++) {
+                dl[0][c] = gv[n][10 + c] / G.hn;
+                dr[0][c] = gv[n][15 + c] / G.hn;
+                d0[0][c] = gv[n][20 + c] / G.hn;
+                dl[1][c] = gd1[n][c] / h1;
+                dr[1][c] = gd1[n][5 + c] / h1;
+                d0[1][c] = gd1[n][10 + c] / h1;
+                dl[2][c] = gd2[n][c] / h2;
+                dr[2][c] = gd2[n][5 + c] / h2;
+                d0[2][c] = gd2[n][10 + c] / h2;
+            }
+            T Fn[5], dFn[5];
+            gks_point_flux<T>(&gv[n][0], &gv[n][5], dl, dr, d0, P, dt, Fn, dFn);
+#pragma unroll
+            for (int c = 0; c < 5; c++) {
+                Fs[c] += 0.25 * Fn[c];
+                dFs[c] += 0.25 * dFn[c];
+            }
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 5; c++) {
+        Fs[c] = Fs[c] * G.area;
+        dFs[c] = dFs[c] * G.area;
+    }
+}
+
+}  // namespace hgks
