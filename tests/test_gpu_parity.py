@@ -215,15 +215,19 @@ def test_full_size_tgv_256(hg, oracle):
     Lc, dLc = c.rhs_cells(dt, cells)
     Lgs = Lg.reshape(5, -1)[:, cells].T
     dLgs = dLg.reshape(5, -1)[:, cells].T
-    # L is a difference of face fluxes of size |Q| (|u| + c) per face, divided by
-    # a cell width: at 256^3 it cancels four to five digits, so the errors are
-    # measured against that flux-divergence scale (rounding acts on it)
+    # L is a difference of face fluxes divided by a cell width: at 256^3 it
+    # cancels four to five digits, so the errors are measured against the
+    # flux-divergence scale (rounding acts on it): mass rho (|u| + c), momenta
+    # |rho u| (|u| + c) + p, energy (rho E + p)(|u| + c), over h
     Qm = np.abs(q).reshape(5, -1).max(axis=1)
     rho, mom = q[0], q[1:4]
     u = np.abs(mom / rho).max()
     pr = (GAMMA - 1) * (q[4] - 0.5 * (mom ** 2).sum(axis=0) / rho)
     cmax = np.sqrt(GAMMA * pr / rho).max()
     h = 2 * np.pi / N
-    S = Qm * (u + cmax) / h
+    S = np.empty(5)
+    S[0] = Qm[0] * (u + cmax) / h
+    S[1:4] = (Qm[1:4].max() * (u + cmax) + pr.max()) / h
+    S[4] = (Qm[4] + pr.max()) * (u + cmax) / h
     assert (np.abs(Lgs - Lc) / S).max() < 1e-13
     assert (np.abs(dLgs - dLc) / (S / dt)).max() < 1e-11
