@@ -188,6 +188,41 @@ typedef struct {
 } hgks_flop_model_t;
 hgks_status hgks_flop_model(const hgks_grid *grid, hgks_precision precision, hgks_flop_model_t *out);
 
+/* Largest grid (cells) accepted by hgks_cfl_dt_noalloc. */
+#define HGKS_NOALLOC_MAX_CELLS 33554432
+
+/* The CFL time step of a caller-owned device state, with no device memory
+ * allocated by this call or by the library (the paper has no counterpart;
+ * this is a library service).
+ *
+ * For callers that cannot allocate device memory when they need a time step:
+ * an application whose memory manager reserved the whole device at start-up,
+ * a solver embedded in another program's time loop that must not change the
+ * device footprint, or a loop that cannot afford the implicit device-wide
+ * synchronisation of cudaMalloc/cudaFree.
+ *
+ *   grid:  cell counts, box lengths and y map as for hgks_create (host, read).
+ *   gamma: ratio of specific heats (> 1).   cfl: CFL number (> 0).
+ *   d_q:   device pointer, the conservative state double[5][nz][ny][nx]
+ *          (no ghost cells), owned by the caller, read only.
+ *   d_dt:  device pointer to one double, owned by the caller; receives
+ *          cfl * min over cells and directions of dx_d / (|u_d| + c).
+ *   cuda_stream: the stream the work is enqueued on (NULL = default stream);
+ *          the call is asynchronous: d_dt holds the result once the stream
+ *          reaches this work.
+ * Scratch: a fixed 1 MiB array of device memory (one double per 256 cells)
+ * that every GPU loading the library holds until the process exits.  Grids
+ * with more than HGKS_NOALLOC_MAX_CELLS cells are rejected with
+ * HGKS_ERR_INVALID_ARG.  Every call uses the same array (it keeps the last
+ * call's partial minima; each call writes every slot it reads), so calls
+ * whose work overlaps on the GPU race with each other: serialise them on one
+ * stream.  The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture begins.
+ * Errors: INVALID_ARG (NULL pointer, bad sizes, too many cells), CUDA. */
+hgks_status hgks_cfl_dt_noalloc(const hgks_grid *grid, double gamma, double cfl, const double *d_q,
+                                double *d_dt, void *cuda_stream);
+
 /* Device bytes a handle for this grid and precision allocates (admission). */
 size_t hgks_footprint_bytes(const hgks_grid *grid, hgks_precision precision);
 

@@ -41,6 +41,11 @@ struct hgks_s {
 
 static thread_local std::string g_err;
 
+namespace hgks {
+// message for hgks_last_error(NULL) from entry points that take no handle
+void set_global_error(const char *msg) { g_err = msg; }
+}  // namespace hgks
+
 static hgks_status set_err(hgks_t h, hgks_status s, const std::string &msg)
 {
     if (h) h->err = msg;

@@ -1,0 +1,168 @@
+// hgks_noalloc.cu -- CFL time step of a caller-owned device state without any
+// device allocation (hgks_cfl_dt_noalloc in include/hgks.h).
+//
+// Some callers cannot allocate device memory when they need a time step: an
+// application whose memory manager reserved every byte of the device at
+// start-up (a fixed arena), a solver embedded in another program's time loop
+// that must not change the device footprint, or a time loop that cannot
+// afford the implicit device-wide synchronisation of cudaMalloc/cudaFree.
+// This entry point therefore keeps its scratch, one partial minimum per
+// 256-cell block, in a fixed file-scope device array.
+//
+// The reduction has two passes: each block writes its minimum of
+// dx_d / (|u_d| + c) into its own slot of the array, then one block folds
+// the slots and writes cfl * min to the caller's output.  Every slot that the
+// second pass reads is written by the first pass of the same call, so
+// nothing has to be cleared between calls.
+#include "../../include/hgks.h"
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <mutex>
+
+namespace hgks {
+void set_global_error(const char *msg);  // hgks_api.cu
+}
+
+namespace {
+
+constexpr int NA_BLOCK = 256;
+// one partial minimum per block of 256 cells: 131072 doubles = 1 MiB, enough
+// for grids up to 256 * 131072 = 33,554,432 cells (for example 320^3)
+constexpr int NA_MAX_BLOCKS = HGKS_NOALLOC_MAX_CELLS / NA_BLOCK;
+static_assert(HGKS_NOALLOC_MAX_CELLS % NA_BLOCK == 0, "cell limit must be a whole number of blocks");
+
+// Lives on every device that loads the library, until the process exits.
+// In host code this name is only a host-side stand-in for the device array:
+// its device address comes from cudaGetSymbolAddress below.
+static __device__ __align__(256) double g_cfl_partials[NA_MAX_BLOCKS];
+
+struct NaGrid {
+    int nx, ny, nz;
+    double hx, hz;
+    double ly, y0, b;  // y map (b = 0: uniform)
+    double gamma;
+    long long ncell;
+};
+
+// physical height of y cell j, from the map of include/hgks.h
+__device__ double na_cell_height(const NaGrid &g, int j)
+{
+    if (!(g.b > 0.0)) return g.ly / g.ny;
+    const double tb = tanh(g.b);
+    const double s0 = 2.0 * j / g.ny, s1 = 2.0 * (j + 1) / g.ny;
+    const double y0 = g.y0 + 0.5 * g.ly * (1.0 + tanh(g.b * (s0 - 1.0)) / tb);
+    const double y1 = g.y0 + 0.5 * g.ly * (1.0 + tanh(g.b * (s1 - 1.0)) / tb);
+    return y1 - y0;
+}
+
+__global__ void __launch_bounds__(NA_BLOCK) k_na_cfl_partial(NaGrid g, const double *__restrict__ q,
+                                                              double *__restrict__ partials)
+{
+    __shared__ double red[NA_BLOCK / 32];
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double v = INFINITY;
+    if (t < g.ncell) {
+        const int j = (int)((t / g.nx) % g.ny);
+        const double rho = q[t], ir = 1.0 / rho;
+        const double U = q[g.ncell + t] * ir, V = q[2 * g.ncell + t] * ir, W = q[3 * g.ncell + t] * ir;
+        const double p = (g.gamma - 1.0) * (q[4 * g.ncell + t] - 0.5 * rho * (U * U + V * V + W * W));
+        const double c = sqrt(g.gamma * p * ir);
+        v = fmin(g.hx / (fabs(U) + c), fmin(na_cell_height(g, j) / (fabs(V) + c), g.hz / (fabs(W) + c)));
+    }
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_down_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        v = threadIdx.x < NA_BLOCK / 32 ? red[threadIdx.x] : INFINITY;
+        for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_down_sync(0xffffffffu, v, o));
+        if (threadIdx.x == 0) partials[blockIdx.x] = v;
+    }
+}
+
+__global__ void __launch_bounds__(NA_BLOCK) k_na_cfl_final(const double *__restrict__ partials, int nblocks,
+                                                            double cfl, double *__restrict__ dt_out)
+{
+    __shared__ double red[NA_BLOCK / 32];
+    double v = INFINITY;
+    for (int b = threadIdx.x; b < nblocks; b += NA_BLOCK) v = fmin(v, partials[b]);
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_down_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        v = threadIdx.x < NA_BLOCK / 32 ? red[threadIdx.x] : INFINITY;
+        for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_down_sync(0xffffffffu, v, o));
+        if (threadIdx.x == 0) *dt_out = cfl * v;
+    }
+}
+
+// device address of g_cfl_partials, looked up once per device with that device current
+constexpr int NA_MAX_DEVICES = 64;
+static double *g_partials_addr[NA_MAX_DEVICES];
+static std::mutex g_setup_mutex;
+
+cudaError_t partials_address(double **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= NA_MAX_DEVICES) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
+    if (!g_partials_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_cfl_partials);
+        if (e != cudaSuccess) return e;
+        g_partials_addr[dev] = (double *)p;
+    }
+    *out = g_partials_addr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" hgks_status hgks_cfl_dt_noalloc(const hgks_grid *grid, double gamma, double cfl, const double *d_q,
+                                           double *d_dt, void *cuda_stream)
+{
+    if (!grid || !d_q || !d_dt) {
+        hgks::set_global_error("hgks_cfl_dt_noalloc: null argument");
+        return HGKS_ERR_INVALID_ARG;
+    }
+    if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1 || !(grid->lx > 0.0) || !(grid->ly > 0.0) ||
+        !(grid->lz > 0.0) || !(gamma > 1.0) || !(cfl > 0.0)) {
+        hgks::set_global_error("hgks_cfl_dt_noalloc: need positive sizes and lengths, gamma > 1, cfl > 0");
+        return HGKS_ERR_INVALID_ARG;
+    }
+    const long long ncell = (long long)grid->nx * grid->ny * grid->nz;
+    if (ncell > HGKS_NOALLOC_MAX_CELLS) {  // beyond the fixed scratch
+        hgks::set_global_error("hgks_cfl_dt_noalloc: the grid has more than HGKS_NOALLOC_MAX_CELLS "
+                               "(33554432) cells, the limit of its fixed scratch");
+        return HGKS_ERR_INVALID_ARG;
+    }
+    double *partials = nullptr;
+    if (partials_address(&partials) != cudaSuccess) {
+        cudaGetLastError();
+        hgks::set_global_error("hgks_cfl_dt_noalloc: cudaGetSymbolAddress of the scratch array failed");
+        return HGKS_ERR_CUDA;
+    }
+    NaGrid g;
+    g.nx = grid->nx;
+    g.ny = grid->ny;
+    g.nz = grid->nz;
+    g.hx = grid->lx / grid->nx;
+    g.hz = grid->lz / grid->nz;
+    g.ly = grid->ly;
+    g.y0 = grid->y0;
+    g.b = grid->y_stretch_b;
+    g.gamma = gamma;
+    g.ncell = ncell;
+    const int nblocks = (int)((ncell + NA_BLOCK - 1) / NA_BLOCK);
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    k_na_cfl_partial<<<nblocks, NA_BLOCK, 0, st>>>(g, d_q, partials);
+    k_na_cfl_final<<<1, NA_BLOCK, 0, st>>>(partials, nblocks, cfl, d_dt);
+    if (cudaGetLastError() != cudaSuccess) {
+        hgks::set_global_error("hgks_cfl_dt_noalloc: kernel launch failed");
+        return HGKS_ERR_CUDA;
+    }
+    return HGKS_OK;
+}

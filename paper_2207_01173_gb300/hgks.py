@@ -81,7 +81,7 @@ _lib = None
 EXPORTS = ("hgks_create", "hgks_init_tgv", "hgks_init_channel", "hgks_init_density_wave", "hgks_set_state",
            "hgks_get_state", "hgks_set_time", "hgks_step", "hgks_step_dt", "hgks_compute_dt", "hgks_rhs",
            "hgks_stats", "hgks_footprint_bytes", "hgks_last_error", "hgks_synchronize", "hgks_destroy",
-           "hgks_step_timed", "hgks_fp64_probe", "hgks_flop_model")
+           "hgks_step_timed", "hgks_fp64_probe", "hgks_flop_model", "hgks_cfl_dt_noalloc")
 
 
 def library_path():
@@ -120,6 +120,8 @@ def lib(build_if_missing=True):
         L.hgks_step_timed.argtypes = [C.c_void_p, C.c_double, C.POINTER(StepTimes)]
         L.hgks_fp64_probe.argtypes = [_D]
         L.hgks_flop_model.argtypes = [C.POINTER(Grid), C.c_int, C.POINTER(FlopModel)]
+        L.hgks_cfl_dt_noalloc.argtypes = [C.POINTER(Grid), C.c_double, C.c_double, C.c_void_p, C.c_void_p,
+                                          C.c_void_p]
         for name in EXPORTS:
             if name not in ("hgks_footprint_bytes", "hgks_last_error", "hgks_destroy"):
                 getattr(L, name).restype = S
@@ -164,6 +166,22 @@ def fp64_probe():
     if st != HGKS_OK:
         raise HgksError(st, lib().hgks_last_error(None).decode())
     return v.value
+
+
+NOALLOC_MAX_CELLS = 33554432
+
+
+def cfl_dt_noalloc(n, d_q, d_dt, cfl=0.5, gamma=1.4, stream=None, **grid_kw):
+    """CFL time step of a caller-owned device state without device allocation.
+
+    d_q, d_dt: device pointers (ints) to double[5][nz][ny][nx] and to one
+    double.  Asynchronous on `stream` (default: PyTorch's current stream).
+    """
+    g = make_grid(n, **grid_kw)
+    st = lib().hgks_cfl_dt_noalloc(C.byref(g), gamma, cfl, C.c_void_p(d_q), C.c_void_p(d_dt),
+                                   stream if stream is not None else _current_stream())
+    if st != HGKS_OK:
+        raise HgksError(st, lib().hgks_last_error(None).decode())
 
 
 def _f64(a, n=None):
