@@ -24,8 +24,9 @@ HGKS_HD void normal_body(Load load, Store store, double K)
         WenoPrep<T> wl, wr;
         weno_prep(X, wl);      // cell f-1
         weno_prep(X + 1, wr);  // cell f
-        T lm_r = weno_edge(wl, 1), lm_l = weno_edge(wl, 0);
-        T r_l = weno_edge(wr, 0), r_r = weno_edge(wr, 1);
+        T lm_l, lm_r, r_l, r_r;
+        weno_edge_pair(wl, lm_l, lm_r);
+        weno_edge_pair(wr, r_l, r_r);
         Ql[c] = lm_r;
         Qr[c] = r_l;
         store(0 * 5 + c, lm_r);
@@ -71,8 +72,10 @@ HGKS_HD void tan1_body(Load load, Store store)
             for (int j = 0; j < 5; j++) X[j] = load(slot * 5 + c, j);
             WenoPrep<T> W;
             weno_prep(X, W);
-            store(0 * 55 + w * 5 + c, weno_gauss(W, 0));
-            store(1 * 55 + w * 5 + c, weno_gauss(W, 1));
+            T vm, vp;
+            weno_gauss_pair(W, vm, vp);
+            store(0 * 55 + w * 5 + c, vm);
+            store(1 * 55 + w * 5 + c, vp);
         }
     }
 #pragma unroll 1
@@ -83,19 +86,21 @@ HGKS_HD void tan1_body(Load load, Store store)
             T X[5];
 #pragma unroll
             for (int j = 0; j < 5; j++) X[j] = load(slot * 5 + c, j);
-#pragma unroll
-            for (int m = 0; m < 2; m++) {
-                store(m * 55 + 25 + l * 5 + c, quartic_value(X, m));
-                store(m * 55 + 40 + l * 5 + c, quartic_deriv(X, m));
-            }
+            T vm, vp, dm, dp;
+            quartic_value_pair(X, vm, vp);
+            quartic_deriv_pair(X, dm, dp);
+            store(0 * 55 + 25 + l * 5 + c, vm);
+            store(1 * 55 + 25 + l * 5 + c, vp);
+            store(0 * 55 + 40 + l * 5 + c, dm);
+            store(1 * 55 + 40 + l * 5 + c, dp);
         }
     }
 }
 
-// geometry of one face: normal metric, tangential metrics at the Gauss
-// abscissae, area
+// geometry of one face: inverse normal metric, inverse tangential metrics at
+// the Gauss abscissae, area
 struct FaceGeom {
-    double hn, h1[2], h2[2], area;
+    double ihn, ih1[2], ih2[2], area;
 };
 
 // second tangential direction, the four Gauss-point fluxes and their sum.
@@ -111,7 +116,7 @@ HGKS_HD void flux_body(Load load, const FaceGeom &G, const Params &P, T dt, T Fs
     }
 #pragma unroll 1
     for (int m = 0; m < 2; m++) {
-        const double h1 = G.h1[m];
+        const double ih1 = G.ih1[m];
         T gv[2][25], gd1[2][15], gd2[2][15];
 #pragma unroll 1
         for (int k = 0; k < 25; k++) {
@@ -120,8 +125,7 @@ HGKS_HD void flux_body(Load load, const FaceGeom &G, const Params &P, T dt, T Fs
             for (int j = 0; j < 5; j++) X[j] = load(m * 55 + k, j);
             WenoPrep<T> W;
             weno_prep(X, W);
-            gv[0][k] = weno_gauss(W, 0);
-            gv[1][k] = weno_gauss(W, 1);
+            weno_gauss_pair(W, gv[0][k], gv[1][k]);
         }
 #pragma unroll 1
         for (int k = 0; k < 15; k++) {
@@ -131,26 +135,24 @@ HGKS_HD void flux_body(Load load, const FaceGeom &G, const Params &P, T dt, T Fs
                 X[j] = load(m * 55 + 40 + k, j);  // first-direction derivatives
                 Y[j] = load(m * 55 + 25 + k, j);  // first-direction quartic values
             }
-            gd1[0][k] = quartic_value(X, 0);
-            gd1[1][k] = quartic_value(X, 1);
-            gd2[0][k] = quartic_deriv(Y, 0);
-            gd2[1][k] = quartic_deriv(Y, 1);
+            quartic_value_pair(X, gd1[0][k], gd1[1][k]);
+            quartic_deriv_pair(Y, gd2[0][k], gd2[1][k]);
         }
 #pragma unroll 1
         for (int n = 0; n < 2; n++) {
-            const double h2 = G.h2[n];
+            const double ih2 = G.ih2[n];
             T dl[3][5], dr[3][5], d0[3][5];
 #pragma unroll
             for (int c = 0; c < 5; c++) {
-                dl[0][c] = gv[n][10 + c] / G.hn;
-                dr[0][c] = gv[n][15 + c] / G.hn;
-                d0[0][c] = gv[n][20 + c] / G.hn;
-                dl[1][c] = gd1[n][c] / h1;
-                dr[1][c] = gd1[n][5 + c] / h1;
-                d0[1][c] = gd1[n][10 + c] / h1;
-                dl[2][c] = gd2[n][c] / h2;
-                dr[2][c] = gd2[n][5 + c] / h2;
-                d0[2][c] = gd2[n][10 + c] / h2;
+                dl[0][c] = gv[n][10 + c] * G.ihn;
+                dr[0][c] = gv[n][15 + c] * G.ihn;
+                d0[0][c] = gv[n][20 + c] * G.ihn;
+                dl[1][c] = gd1[n][c] * ih1;
+                dr[1][c] = gd1[n][5 + c] * ih1;
+                d0[1][c] = gd1[n][10 + c] * ih1;
+                dl[2][c] = gd2[n][c] * ih2;
+                dr[2][c] = gd2[n][5 + c] * ih2;
+                d0[2][c] = gd2[n][10 + c] * ih2;
             }
             T Fn[5], dFn[5];
             gks_point_flux<T>(&gv[n][0], &gv[n][5], dl, dr, d0, P, dt, Fn, dFn);

@@ -11,8 +11,10 @@
 //     the closed forms below (derived symbolically from cell averages).
 //   * Maxwellian moments <u^n> by <u^{n+2}> = U <u^{n+1}> + (n+1)/(2 lambda) <u^n>,
 //     half-range starts 1/2 erfc(-+sqrt(lambda) U) and e^{-lambda U^2}/(2 sqrt(pi lambda)).
-//   * micro-slopes from the moment equations solved in central variables
-//     c = u - U (closed-form inverse of the 5x5 moment matrix).
+//   * the micro-slope terms of the flux (a g = dg/dQ . dQ for a Maxwellian)
+//     as directional derivatives of moment functions: Euler-flux Jacobians for
+//     the full-range equilibrium terms, differentiated half-range moments for
+//     the l/r terms, so no 5x5 slope system is ever solved.
 // The arithmetic routines are templates on the scalar type T (double on the
 // device; a host operation-counting type instantiates the same code to count
 // the scheme's floating-point work).
@@ -87,43 +89,53 @@ struct WenoPrep {
 template <typename T>
 HGKS_HD void weno_prep(const T X[5], WenoPrep<T> &W)
 {
+    // candidate slopes and curvatures from the first differences of the averages
+    const T d1 = X[1] - X[0], d2 = X[2] - X[1], d3 = X[3] - X[2], d4 = X[4] - X[3];
     W.x0 = X[2];
-    W.c2[0] = 0.5 * (X[0] - 2.0 * X[1] + X[2]);
-    W.c1[0] = 0.5 * (X[0] - 4.0 * X[1] + 3.0 * X[2]);
-    W.c2[1] = 0.5 * (X[1] - 2.0 * X[2] + X[3]);
-    W.c1[1] = 0.5 * (X[3] - X[1]);
-    W.c2[2] = 0.5 * (X[2] - 2.0 * X[3] + X[4]);
-    W.c1[2] = 0.5 * (-3.0 * X[2] + 4.0 * X[3] - X[4]);
+    W.c2[0] = 0.5 * (d2 - d1);
+    W.c1[0] = 1.5 * d2 - 0.5 * d1;
+    W.c2[1] = 0.5 * (d3 - d2);
+    W.c1[1] = 0.5 * (d3 + d2);
+    W.c2[2] = 0.5 * (d4 - d3);
+    W.c1[2] = 1.5 * d3 - 0.5 * d4;
     T b[3];
 #pragma unroll
     for (int k = 0; k < 3; k++) b[k] = W.c1[k] * W.c1[k] + (13.0 / 3.0) * W.c2[k] * W.c2[k] + WENO_EPS;
     T tau5 = fabs(b[0] - b[2]);
-    W.cw[0] = (b[0] + tau5) * b[1] * b[2];
-    W.cw[1] = (b[1] + tau5) * b[0] * b[2];
-    W.cw[2] = (b[2] + tau5) * b[0] * b[1];
+    W.cw[0] = (b[0] + tau5) * (b[1] * b[2]);
+    W.cw[1] = (b[1] + tau5) * (b[0] * b[2]);
+    W.cw[2] = (b[2] + tau5) * (b[0] * b[1]);
 }
 
-// value at the right (+1/2) or left (-1/2) cell edge; linear weights (1,6,3)/10 mirrored
+// both Gauss abscissae from one reciprocal: the two denominators D- and D+
+// (mirrored linear weights) are inverted together as 1/(D- D+)
 template <typename T>
-HGKS_HD T weno_edge(const WenoPrep<T> &W, int right)
+HGKS_HD void weno_gauss_pair(const WenoPrep<T> &W, T &vm, T &vp)
 {
-    double d0 = right ? 0.1 : 0.3, d2 = right ? 0.3 : 0.1, s = right ? 0.5 : -0.5;
-    T a0 = d0 * W.cw[0], a1 = 0.6 * W.cw[1], a2 = d2 * W.cw[2];
-    T p0 = W.x0 + s * W.c1[0] + W.c2[0] * (1.0 / 6.0);
-    T p1 = W.x0 + s * W.c1[1] + W.c2[1] * (1.0 / 6.0);
-    T p2 = W.x0 + s * W.c1[2] + W.c2[2] * (1.0 / 6.0);
-    return (a0 * p0 + a1 * p1 + a2 * p2) / (a0 + a1 + a2);
+    const T e0 = HGKS_DGL * W.cw[0], e2 = HGKS_DGR * W.cw[2], f0 = HGKS_DGR * W.cw[0], f2 = HGKS_DGL * W.cw[2];
+    const T a1 = HGKS_DGC * W.cw[1];
+    const T dp = e0 + a1 + e2, dm = f0 + a1 + f2;  // plus: (DGL, DGC, DGR), minus: mirrored
+    const T np = e0 * W.c1[0] + a1 * W.c1[1] + e2 * W.c1[2];
+    const T nm = f0 * W.c1[0] + a1 * W.c1[1] + f2 * W.c1[2];
+    const T r = 1.0 / (dp * dm);
+    vp = W.x0 + HGKS_GAUSS * (np * dm * r);
+    vm = W.x0 - HGKS_GAUSS * (nm * dp * r);
 }
 
-// value at the Gauss abscissa -sqrt(3)/6 (plus = 0) or +sqrt(3)/6 (plus = 1)
+// both cell edges (-1/2: vl, +1/2: vr) from one reciprocal
 template <typename T>
-HGKS_HD T weno_gauss(const WenoPrep<T> &W, int plus)
+HGKS_HD void weno_edge_pair(const WenoPrep<T> &W, T &vl, T &vr)
 {
-    double d0 = plus ? HGKS_DGL : HGKS_DGR, d2 = plus ? HGKS_DGR : HGKS_DGL;
-    double s = plus ? HGKS_GAUSS : -HGKS_GAUSS;
-    T a0 = d0 * W.cw[0], a1 = HGKS_DGC * W.cw[1], a2 = d2 * W.cw[2];
-    T num = a0 * W.c1[0] + a1 * W.c1[1] + a2 * W.c1[2];
-    return W.x0 + s * num / (a0 + a1 + a2);
+    const T a1 = 0.6 * W.cw[1];
+    const T r0 = 0.1 * W.cw[0], r2 = 0.3 * W.cw[2];  // right edge weights
+    const T l0 = 0.3 * W.cw[0], l2 = 0.1 * W.cw[2];  // left edge weights
+    const T p0 = W.x0 + W.c2[0] * (1.0 / 6.0), p1 = W.x0 + W.c2[1] * (1.0 / 6.0), p2 = W.x0 + W.c2[2] * (1.0 / 6.0);
+    const T nr = r0 * (p0 + 0.5 * W.c1[0]) + a1 * (p1 + 0.5 * W.c1[1]) + r2 * (p2 + 0.5 * W.c1[2]);
+    const T nl = l0 * (p0 - 0.5 * W.c1[0]) + a1 * (p1 - 0.5 * W.c1[1]) + l2 * (p2 - 0.5 * W.c1[2]);
+    const T dr = r0 + a1 + r2, dl = l0 + a1 + l2;
+    const T r = 1.0 / (dr * dl);
+    vr = nr * dl * r;
+    vl = nl * dr * r;
 }
 
 // quartic through five cell averages: point value and derivative (index units)
@@ -133,18 +145,20 @@ HGKS_HD T weno_gauss(const WenoPrep<T> &W, int plus)
 // deriv = C.X -+ sqrt3 S.X,  C = (1/12, -2/3, 0, 2/3, -1/12),
 //                           S = (1/54, -13/54, 24/54, -13/54, 1/54)
 template <typename T>
-HGKS_HD T quartic_value(const T X[5], int plus)
+HGKS_HD void quartic_value_pair(const T X[5], T &vm, T &vp)
 {
-    T e = (-1.0 / 4320.0) * (X[0] + X[4]) + (1.0 / 1080.0) * (X[1] + X[3]) + (719.0 / 720.0) * X[2];
-    T o = (7.0 / 432.0) * (X[0] - X[4]) + (25.0 / 216.0) * (X[3] - X[1]);
-    return plus ? e + HGKS_SQ3 * o : e - HGKS_SQ3 * o;
+    const T e = (-1.0 / 4320.0) * (X[0] + X[4]) + (1.0 / 1080.0) * (X[1] + X[3]) + (719.0 / 720.0) * X[2];
+    const T o = HGKS_SQ3 * ((7.0 / 432.0) * (X[0] - X[4]) + (25.0 / 216.0) * (X[3] - X[1]));
+    vm = e - o;
+    vp = e + o;
 }
 template <typename T>
-HGKS_HD T quartic_deriv(const T X[5], int plus)
+HGKS_HD void quartic_deriv_pair(const T X[5], T &dm, T &dp)
 {
-    T c = (1.0 / 12.0) * (X[0] - X[4]) + (2.0 / 3.0) * (X[3] - X[1]);
-    T s = (1.0 / 54.0) * (X[0] + X[4]) - (13.0 / 54.0) * (X[1] + X[3]) + (24.0 / 54.0) * X[2];
-    return plus ? c - HGKS_SQ3 * s : c + HGKS_SQ3 * s;
+    const T c = (1.0 / 12.0) * (X[0] - X[4]) + (2.0 / 3.0) * (X[3] - X[1]);
+    const T s = HGKS_SQ3 * ((1.0 / 54.0) * (X[0] + X[4]) - (13.0 / 54.0) * (X[1] + X[3]) + (24.0 / 54.0) * X[2]);
+    dm = c + s;
+    dp = c - s;
 }
 
 // ---------------------------------------------------------------------------
@@ -219,75 +233,300 @@ HGKS_HD void psi_mom(const Mom<T> &m, T o[5])
                   + uvw * m.xi1);
 }
 
-// <a(u) psi_i u^A v^B w^C>, a(u) = a0 + a1 u + a2 v + a3 w + a4 (u^2 + v^2 + w^2 + xi^2)/2
-template <int A, int B, int C, typename T>
-HGKS_HD void mom_a(const Mom<T> &m, const T a[5], T o[5])
-{
-    T t[5];
-    psi_mom<A, B, C>(m, t);
-#pragma unroll
-    for (int i = 0; i < 5; i++) o[i] = a[0] * t[i];
-    psi_mom<A + 1, B, C>(m, t);
-#pragma unroll
-    for (int i = 0; i < 5; i++) o[i] += a[1] * t[i];
-    psi_mom<A, B + 1, C>(m, t);
-#pragma unroll
-    for (int i = 0; i < 5; i++) o[i] += a[2] * t[i];
-    psi_mom<A, B, C + 1>(m, t);
-#pragma unroll
-    for (int i = 0; i < 5; i++) o[i] += a[3] * t[i];
-    // psi_5 part: (u^2 + v^2 + w^2)/2 and xi^2/2
-    T s[5];
-    psi_mom<A + 2, B, C>(m, t);
-#pragma unroll
-    for (int i = 0; i < 5; i++) s[i] = t[i];
-    psi_mom<A, B + 2, C>(m, t);
-#pragma unroll
-    for (int i = 0; i < 5; i++) s[i] += t[i];
-    psi_mom<A, B, C + 2>(m, t);
-#pragma unroll
-    for (int i = 0; i < 5; i++) s[i] += t[i];
-    // xi^2 psi_i u^A v^B w^C: psi_0..3 carry no xi; psi_4 carries xi^2/2
-    psi_mom<A, B, C>(m, t);
-    T uvw = m.u[A] * m.v[B] * m.w[C];
-#pragma unroll
-    for (int i = 0; i < 4; i++) s[i] += m.xi1 * t[i];
-    s[4] += 0.5 * (m.xi1 * (m.u[A + 2] * m.v[B] * m.w[C] + m.u[A] * m.v[B + 2] * m.w[C]
-                            + m.u[A] * m.v[B] * m.w[C + 2]) + m.xi2 * uvw);
-#pragma unroll
-    for (int i = 0; i < 5; i++) o[i] += 0.5 * a[4] * s[i];
-}
-
-// <a psi> = rho b for a Maxwellian (U, V, W, lambda):
-// a5 = 8 lam^2/(K+3) (b5 - U.b_mom + b1 (|U|^2 - E)),  E = |U|^2/2 + (K+3)/(4 lam)
-// a2..4 = 2 lam (b_mom - U b1) - a5 U,  a1 = b1 - U.a_mom - a5 E
-template <typename T>
-HGKS_HD void micro_slope(const T b[5], const Prim<T> &g, double K, T a[5])
-{
-    T uu = g.U * g.U + g.V * g.V + g.W * g.W;
-    T E = 0.5 * uu + (K + 3.0) / (4.0 * g.lam);
-    T tl = 2.0 * g.lam;
-    a[4] = 2.0 * tl * tl / (K + 3.0) * (b[4] - g.U * b[1] - g.V * b[2] - g.W * b[3] + b[0] * (uu - E));
-    a[1] = tl * (b[1] - g.U * b[0]) - a[4] * g.U;
-    a[2] = tl * (b[2] - g.V * b[0]) - a[4] * g.V;
-    a[3] = tl * (b[3] - g.W * b[0]) - a[4] * g.W;
-    a[0] = b[0] - g.U * a[1] - g.V * a[2] - g.W * a[3] - a[4] * E;
-}
-
 template <typename T>
 HGKS_HD T viscosity(const Params &P, T Tm)
 {
     return P.visc_kind == 1 ? P.mu_ref * pow(Tm / P.T_ref, P.omega) : T(P.mu_ref);
 }
 
-// heat flux about U0 of a term with flux moments B (of u psi) and moments W (of psi):
-// q = int (u - U0) (|c|^2 + xi^2)/2 f, c = velocity relative to (U0, V0, W0)
+// ---------------------------------------------------------------------------
+// flux-economic form of the point flux
+// ---------------------------------------------------------------------------
+// A Maxwellian g(Q) and the micro-slope a of a change dQ of its conserved
+// variables satisfy a g = (dg/dQ) dQ.  Full-range moments of a g are therefore
+// directional derivatives of moment functions of the Maxwellian:
+//   sum_d <psi u_d a_d> rho = sum_d DF_d(Q)[d_d Q]    (F_d the Euler flux)
+//   sum_d <psi u u_d a_d> rho = sum_d DH_d(Q)[d_d Q]  (H_d = rho <psi u u_d>)
+//   <psi u A> rho = DF_n(Q)[d_t Q],  <psi A> rho = d_t Q,
+// with d_t Q = -sum_d DF_d(Q)[d_d Q] from <a.u + A> = 0.  These closed forms
+// replace the generic moment sums for the equilibrium terms; the half-range
+// (u > 0, u < 0) terms keep the moment sums.
+
+// primitive and derived quantities of one Maxwellian (R = 1)
 template <typename T>
-HGKS_HD T heat_of(const T B[5], const T W[5], const Prim<T> &g0)
+struct Gas {
+    T rho, ir, U[3], uu, p, Tm, tl, lam, E;  // tl = 2 lambda = 1/T, E = rho E
+};
+
+template <typename T>
+HGKS_HD Gas<T> gas_of(const T Q[5], double gm1)
 {
-    T U0 = g0.U, V0 = g0.V, W0 = g0.W, uu = U0 * U0 + V0 * V0 + W0 * W0;
+    Gas<T> g;
+    g.rho = Q[0];
+    g.ir = 1.0 / Q[0];
+    g.U[0] = Q[1] * g.ir;
+    g.U[1] = Q[2] * g.ir;
+    g.U[2] = Q[3] * g.ir;
+    g.uu = g.U[0] * g.U[0] + g.U[1] * g.U[1] + g.U[2] * g.U[2];
+    g.E = Q[4];
+    g.p = gm1 * (Q[4] - 0.5 * Q[0] * g.uu);
+    g.Tm = g.p * g.ir;
+    g.tl = 1.0 / g.Tm;
+    g.lam = 0.5 * g.tl;
+    return g;
+}
+
+// directional derivative of the Euler flux F_D (D = 0 normal, 1, 2) along dQ
+template <int D, typename T>
+HGKS_HD void euler_dflux(const Gas<T> &g, const T dQ[5], double gm1, T o[5])
+{
+    const T dp = gm1 * (dQ[4] - (g.U[0] * dQ[1] + g.U[1] * dQ[2] + g.U[2] * dQ[3]) + 0.5 * g.uu * dQ[0]);
+    const T dUd = (dQ[1 + D] - g.U[D] * dQ[0]) * g.ir;
+    o[0] = dQ[1 + D];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        T v = g.U[k] * dQ[1 + D] + g.U[D] * (dQ[1 + k] - g.U[k] * dQ[0]);
+        o[1 + k] = k == D ? v + dp : v;
+    }
+    o[4] = dUd * (g.E + g.p) + g.U[D] * (dQ[4] + dp);
+}
+
+// directional derivative of H_D = rho <psi u u_D> (u the normal velocity):
+// H_D = (rho U Ud + p d0D,
+//        rho U Ud U_k + p (d0D U_k + d0k Ud + dDk U),
+//        U Ud (rho E + 2p) + d0D p (|U|^2 + (K+5) T) / 2)
+template <int D, typename T>
+HGKS_HD void second_dmoment(const Gas<T> &g, const T dQ[5], double gm1, double Kp5, T o[5])
+{
+    const T drho = dQ[0];
+    T dU[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) dU[k] = (dQ[1 + k] - g.U[k] * drho) * g.ir;
+    const T dp = gm1 * (dQ[4] - (g.U[0] * dQ[1] + g.U[1] * dQ[2] + g.U[2] * dQ[3]) + 0.5 * g.uu * drho);
+    const T Un = g.U[0], Ud = g.U[D], dUn = dU[0], dUd = dU[D];
+    const T dUnUd = dUn * Ud + Un * dUd;  // d(Un Ud)
+    const T UnUd = Un * Ud;
+    o[0] = drho * UnUd + g.rho * dUnUd;
+    if (D == 0) o[0] += dp;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        T v = (drho * UnUd + g.rho * dUnUd) * g.U[k] + g.rho * UnUd * dU[k];
+        if (D == 0) v += dp * g.U[k] + g.p * dU[k];
+        if (k == 0) v += dp * Ud + g.p * dUd;
+        if (k == D) v += dp * Un + g.p * dUn;
+        o[1 + k] = v;
+    }
+    o[4] = dUnUd * (g.E + 2.0 * g.p) + UnUd * (dQ[4] + 2.0 * dp);
+    if (D == 0) {
+        const T UdU = g.U[0] * dU[0] + g.U[1] * dU[1] + g.U[2] * dU[2];
+        o[4] += 0.5 * (dp * (g.uu + Kp5 * g.Tm) + g.p * (2.0 * UdU + Kp5 * (dp - g.Tm * drho) * g.ir));
+    }
+}
+
+template <typename T>
+HGKS_HD T heat_of_g(const T B[5], const T W[5], const Gas<T> &g0)
+{
+    const T U0 = g0.U[0], V0 = g0.U[1], W0 = g0.U[2], uu = g0.uu;
     return B[4] - U0 * B[1] - V0 * B[2] - W0 * B[3] + 0.5 * uu * B[0]
          - U0 * W[4] + U0 * U0 * W[1] + U0 * V0 * W[2] + U0 * W0 * W[3] - 0.5 * U0 * uu * W[0];
+}
+
+// ---------------------------------------------------------------------------
+// half-range moments by differentiation
+// ---------------------------------------------------------------------------
+// For a half-range Maxwellian (u > 0: sigma = +1, u < 0: sigma = -1) the
+// micro-slope terms are directional derivatives of half-range moment
+// functions Phi_m(Q) = rho <m psi>_sigma of monomials m (the range boundary
+// u = 0 does not move), so neither a nor A has to be solved for:
+//   <m psi a_d> rho = DPhi_m(Q)[d_d Q],   <m psi A> rho = DPhi_m(Q)[d_t Q].
+// In primitives P = (rho, U, V, W, T) (T = 1/(2 lambda) = p/rho):
+//   M_n (half, normal velocity), with phi0 = exp(-U^2/(2T)) / sqrt(2 pi T):
+//     M_0 = erfc(-sigma U / sqrt(2T)) / 2,  M_1 = U M_0 + sigma T phi0,
+//     M_{n+2} = U M_{n+1} + (n+1) T M_n,
+//     dM_n/dU = n M_{n-1} + sigma phi0 [n = 0],
+//     dM_n/dT = n(n-1)/2 M_{n-2} + sigma phi0 / 2 [n = 1] - sigma U phi0 / (2T) [n = 0];
+//   full-range tangential moments: dM_n/dV = n M_{n-1}, dM_n/dT = n(n-1)/2 M_{n-2};
+//   <xi^2> = K T.
+
+template <typename T>
+struct HalfSide {
+    T rho, ir, U[3], uu, Tm, E, p;
+    T u[5], v[4], w[4], xi1;              // moments (u: half range)
+    T uU[5], uT[5], vV[4], vT[4], wW[4], wT[4];  // their partial derivatives
+};
+
+template <typename T>
+HGKS_HD void half_side_setup(const T Q[5], double gm1, double K, bool pos, HalfSide<T> &h)
+{
+    h.rho = Q[0];
+    h.ir = 1.0 / Q[0];
+    h.U[0] = Q[1] * h.ir;
+    h.U[1] = Q[2] * h.ir;
+    h.U[2] = Q[3] * h.ir;
+    h.uu = h.U[0] * h.U[0] + h.U[1] * h.U[1] + h.U[2] * h.U[2];
+    h.E = Q[4];
+    h.p = gm1 * (Q[4] - 0.5 * Q[0] * h.uu);
+    h.Tm = h.p * h.ir;
+    const double sg = pos ? 1.0 : -1.0;
+    const double inv_sqrt2pi = 0.39894228040143267794;  // 1/sqrt(2 pi)
+    const T iTm = 1.0 / h.Tm;
+    const T isq = sqrt(iTm);                              // 1/sqrt(T)
+    const T U = h.U[0];
+    const T phi0 = exp(-0.5 * U * U * iTm) * (inv_sqrt2pi * isq);
+    h.u[0] = 0.5 * erfc((-sg * 0.70710678118654752440) * U * isq);
+    h.u[1] = U * h.u[0] + sg * h.Tm * phi0;
+#pragma unroll
+    for (int n = 0; n < 3; n++) h.u[n + 2] = U * h.u[n + 1] + (double)(n + 1) * h.Tm * h.u[n];
+    h.uU[0] = sg * phi0;
+    h.uT[0] = (-0.5 * sg) * U * iTm * phi0;
+    h.uU[1] = h.u[0];
+    h.uT[1] = (0.5 * sg) * phi0;
+#pragma unroll
+    for (int n = 2; n < 5; n++) {
+        h.uU[n] = (double)n * h.u[n - 1];
+        h.uT[n] = (0.5 * n * (n - 1)) * h.u[n - 2];
+    }
+    mom_full<4>(h.U[1], h.Tm, h.v);
+    mom_full<4>(h.U[2], h.Tm, h.w);
+    h.vV[0] = 0.0;
+    h.wW[0] = 0.0;
+    h.vT[0] = 0.0;
+    h.wT[0] = 0.0;
+    h.vT[1] = 0.0;
+    h.wT[1] = 0.0;
+#pragma unroll
+    for (int n = 1; n < 4; n++) {
+        h.vV[n] = (double)n * h.v[n - 1];
+        h.wW[n] = (double)n * h.w[n - 1];
+    }
+#pragma unroll
+    for (int n = 2; n < 4; n++) {
+        h.vT[n] = (0.5 * n * (n - 1)) * h.v[n - 2];
+        h.wT[n] = (0.5 * n * (n - 1)) * h.w[n - 2];
+    }
+    h.xi1 = K * h.Tm;
+}
+
+// value of Phi_m = rho <u^E v^J w^L psi>_sigma
+template <int E, int J, int L, typename T>
+HGKS_HD void half_phi(const HalfSide<T> &h, T o[5])
+{
+    const T bc = h.v[J] * h.w[L];
+    const T abc = h.u[E] * bc;
+    o[0] = h.rho * abc;
+    o[1] = h.rho * (h.u[E + 1] * bc);
+    o[2] = h.rho * (h.u[E] * h.v[J + 1] * h.w[L]);
+    o[3] = h.rho * (h.u[E] * h.v[J] * h.w[L + 1]);
+    o[4] = (0.5 * h.rho) * (h.u[E + 2] * bc + h.u[E] * (h.v[J + 2] * h.w[L] + h.v[J] * h.w[L + 2]) + h.xi1 * abc);
+}
+
+// changes of the primitives and of the 1-D moments along a change dQ of the
+// conserved variables
+template <typename T>
+struct HalfDelta {
+    T rho, du[5], dv[4], dw[4], dxi1;
+};
+
+template <typename T>
+HGKS_HD void half_delta(const HalfSide<T> &h, const T dQ[5], double gm1, double K, HalfDelta<T> &d)
+{
+    const T dU = (dQ[1] - h.U[0] * dQ[0]) * h.ir;
+    const T dV = (dQ[2] - h.U[1] * dQ[0]) * h.ir;
+    const T dW = (dQ[3] - h.U[2] * dQ[0]) * h.ir;
+    const T dp = gm1 * (dQ[4] - (h.U[0] * dQ[1] + h.U[1] * dQ[2] + h.U[2] * dQ[3]) + 0.5 * h.uu * dQ[0]);
+    const T dT = (dp - h.Tm * dQ[0]) * h.ir;
+    d.rho = dQ[0];
+#pragma unroll
+    for (int n = 0; n < 5; n++) d.du[n] = h.uU[n] * dU + h.uT[n] * dT;
+#pragma unroll
+    for (int n = 0; n < 4; n++) {
+        d.dv[n] = h.vV[n] * dV + h.vT[n] * dT;
+        d.dw[n] = h.wW[n] * dW + h.wT[n] * dT;
+    }
+    d.dxi1 = K * dT;
+}
+
+// directional derivative of Phi_m along the change d (product rule)
+template <int E, int J, int L, typename T>
+HGKS_HD void half_dphi(const HalfSide<T> &h, const HalfDelta<T> &d, T o[5])
+{
+    // D(rho a b c) = drho abc + rho (da bc + a (db c + b dc))
+    auto prod = [&](const T &a, const T &da, const T &b, const T &db, const T &c, const T &dc, T &val) -> T {
+        const T bc = b * c, dbc = db * c + b * dc;
+        val = a * bc;
+        return d.rho * val + h.rho * (da * bc + a * dbc);
+    };
+    T v0, v1, v2, v3, v4, v5, v6;
+    o[0] = prod(h.u[E], d.du[E], h.v[J], d.dv[J], h.w[L], d.dw[L], v0);
+    o[1] = prod(h.u[E + 1], d.du[E + 1], h.v[J], d.dv[J], h.w[L], d.dw[L], v1);
+    o[2] = prod(h.u[E], d.du[E], h.v[J + 1], d.dv[J + 1], h.w[L], d.dw[L], v2);
+    o[3] = prod(h.u[E], d.du[E], h.v[J], d.dv[J], h.w[L + 1], d.dw[L + 1], v3);
+    const T p4 = prod(h.u[E + 2], d.du[E + 2], h.v[J], d.dv[J], h.w[L], d.dw[L], v4);
+    const T p5 = prod(h.u[E], d.du[E], h.v[J + 2], d.dv[J + 2], h.w[L], d.dw[L], v5);
+    const T p6 = prod(h.u[E], d.du[E], h.v[J], d.dv[J], h.w[L + 2], d.dw[L + 2], v6);
+    // xi^2 term: D(rho xi1 abc) = xi1 D(rho abc) + rho abc dxi1
+    o[4] = 0.5 * (p4 + p5 + p6 + h.xi1 * o[0] + h.rho * v0 * d.dxi1);
+}
+
+// time change of the conserved variables of an Euler state: d_t Q = -sum_d DF_d(Q)[d_d Q]
+template <typename T>
+HGKS_HD void euler_dtq(const Gas<T> &g, const T dq[3][5], double gm1, T o[5])
+{
+    T s[5];
+    euler_dflux<0>(g, dq[0], gm1, o);
+    euler_dflux<1>(g, dq[1], gm1, s);
+#pragma unroll
+    for (int c = 0; c < 5; c++) o[c] += s[c];
+    euler_dflux<2>(g, dq[2], gm1, s);
+#pragma unroll
+    for (int c = 0; c < 5; c++) o[c] = -(o[c] + s[c]);
+}
+
+// all half-range terms of one side: Q0 part and B4 (values), W5, B5 (slopes),
+// W6, B6 (time slope), summed over the three derivative directions
+template <typename T>
+HGKS_HD void half_terms(const T Q[5], const T dq[3][5], double gm1, double K, bool pos, T q0[5], T b4[5],
+                        T w5[5], T b5[5], T w6[5], T b6[5])
+{
+    HalfSide<T> h;
+    half_side_setup(Q, gm1, K, pos, h);
+    half_phi<0, 0, 0>(h, q0);
+    half_phi<1, 0, 0>(h, b4);
+    HalfDelta<T> dd;
+    T s[5];
+    half_delta(h, dq[0], gm1, K, dd);  // normal direction: m = u (W5), u^2 (B5)
+    half_dphi<1, 0, 0>(h, dd, w5);
+    half_dphi<2, 0, 0>(h, dd, b5);
+    half_delta(h, dq[1], gm1, K, dd);  // first tangential: m = v, u v
+    half_dphi<0, 1, 0>(h, dd, s);
+#pragma unroll
+    for (int c = 0; c < 5; c++) w5[c] += s[c];
+    half_dphi<1, 1, 0>(h, dd, s);
+#pragma unroll
+    for (int c = 0; c < 5; c++) b5[c] += s[c];
+    half_delta(h, dq[2], gm1, K, dd);  // second tangential: m = w, u w
+    half_dphi<0, 0, 1>(h, dd, s);
+#pragma unroll
+    for (int c = 0; c < 5; c++) w5[c] += s[c];
+    half_dphi<1, 0, 1>(h, dd, s);
+#pragma unroll
+    for (int c = 0; c < 5; c++) b5[c] += s[c];
+    // time slope of the side's Maxwellian
+    Gas<T> g;
+    g.rho = h.rho;
+    g.ir = h.ir;
+    g.U[0] = h.U[0];
+    g.U[1] = h.U[1];
+    g.U[2] = h.U[2];
+    g.uu = h.uu;
+    g.E = h.E;
+    g.p = h.p;
+    g.Tm = h.Tm;
+    T dtq[5];
+    euler_dtq(g, dq, gm1, dtq);
+    half_delta(h, dtq, gm1, K, dd);
+    half_dphi<0, 0, 0>(h, dd, w6);
+    half_dphi<1, 0, 0>(h, dd, b6);
 }
 
 // GKS flux through a unit-area point of an interface (rotated frame: velocity
@@ -295,176 +534,86 @@ HGKS_HD T heat_of(const T B[5], const T W[5], const Prim<T> &g0)
 // conservative variables along (normal, t1, t2).  Writes F^n and dF^n/dt
 // obtained from the time integrals over [0, dt] and [0, dt/2] (Eq. "expansion-1").
 template <typename T>
-__host__ __device__ __noinline__ void gks_point_flux(const T Ql[5], const T Qr[5], const T dl[3][5], const T dr[3][5],
-                                                     const T d0[3][5], const Params &P, T dt, T Fn[5], T dFn[5])
+__host__ __device__ __noinline__ void gks_point_flux(const T Ql[5], const T Qr[5], const T dl[3][5],
+                                                          const T dr[3][5], const T d0[3][5], const Params &P, T dt,
+                                                          T Fn[5], T dFn[5])
 {
-    const double K = P.K;
-    Prim<T> gl = prim_of(Ql, K), gr = prim_of(Qr, K);
-    T il = 0.5 / gl.lam, ir = 0.5 / gr.lam;
-    T ulf[7], ulp[7], vl[6], wl[6], urf[7], urn[7], vr[6], wr[6];
-    mom_full<7>(gl.U, il, ulf);
-    mom_half<7>(gl.U, gl.lam, il, true, ulp);
-    mom_full<6>(gl.V, il, vl);
-    mom_full<6>(gl.W, il, wl);
-    mom_full<7>(gr.U, ir, urf);
-    mom_half<7>(gr.U, gr.lam, ir, false, urn);
-    mom_full<6>(gr.V, ir, vr);
-    mom_full<6>(gr.W, ir, wr);
-    Mom<T> Ml_f{ulf, vl, wl, K * il, K * (K + 2.0) * il * il};
-    Mom<T> Ml_p{ulp, vl, wl, Ml_f.xi1, Ml_f.xi2};
-    Mom<T> Mr_f{urf, vr, wr, K * ir, K * (K + 2.0) * ir * ir};
-    Mom<T> Mr_n{urn, vr, wr, Mr_f.xi1, Mr_f.xi2};
-
+    const double gm1 = P.gamma - 1.0, K = P.K;
+    const Gas<T> gl = gas_of(Ql, gm1), gr = gas_of(Qr, gm1);
+    // half-range terms of the two sides (values and directional derivatives)
+    T ql[5], b4l[5], w5l[5], b5l[5], w6l[5], b6l[5], qr[5], b4r[5], w5r[5], b5r[5], w6r[5], b6r[5];
+    half_terms(Ql, dl, gm1, K, true, ql, b4l, w5l, b5l, w6l, b6l);
+    half_terms(Qr, dr, gm1, K, false, qr, b4r, w5r, b5r, w6r, b6r);
     // equilibrium state from the compatibility condition
-    T Q0[5], t5[5];
-    psi_mom<0, 0, 0>(Ml_p, Q0);
-    psi_mom<0, 0, 0>(Mr_n, t5);
+    T Q0[5];
 #pragma unroll
-    for (int i = 0; i < 5; i++) Q0[i] = gl.rho * Q0[i] + gr.rho * t5[i];
-    Prim<T> g0 = prim_of(Q0, K);
-    T i0 = 0.5 / g0.lam;
-    T u0[7], v0[6], w0[6];
-    mom_full<7>(g0.U, i0, u0);
-    mom_full<6>(g0.V, i0, v0);
-    mom_full<6>(g0.W, i0, w0);
-    Mom<T> M0{u0, v0, w0, K * i0, K * (K + 2.0) * i0 * i0};
-    const T T0 = i0, p0 = g0.rho * i0;
-    const T tau = viscosity(P, T0) / p0;
+    for (int i = 0; i < 5; i++) Q0[i] = ql[i] + qr[i];
+    const Gas<T> g0 = gas_of(Q0, gm1);
+    const T tau = viscosity(P, g0.Tm) / g0.p;
 
-    // spatial micro-slopes a = M^{-1} dQ / rho
-    T al[3][5], ar[3][5], ab[3][5];
+    // equilibrium terms: B1 = F_n(Q0), B2 = sum_d DH_d(Q0)[d_d Q0], B3 = DF_n(Q0)[d_t Q0],
+    // W2 = -d_t Q0 = R0, W3 = d_t Q0
+    T B1[5], B2[5], B3[5], R0[5];
     {
-        const T rl = 1.0 / gl.rho, rr = 1.0 / gr.rho, r0 = 1.0 / g0.rho;
+        T s[5];
+        B1[0] = Q0[1];
+        B1[1] = Q0[1] * g0.U[0] + g0.p;
+        B1[2] = Q0[1] * g0.U[1];
+        B1[3] = Q0[1] * g0.U[2];
+        B1[4] = g0.U[0] * (g0.E + g0.p);
+        euler_dflux<0>(g0, d0[0], gm1, R0);
+        euler_dflux<1>(g0, d0[1], gm1, s);
 #pragma unroll
-        for (int d = 0; d < 3; d++) {
-            T b[5];
+        for (int c = 0; c < 5; c++) R0[c] += s[c];
+        euler_dflux<2>(g0, d0[2], gm1, s);
 #pragma unroll
-            for (int c = 0; c < 5; c++) b[c] = dl[d][c] * rl;
-            micro_slope(b, gl, K, al[d]);
+        for (int c = 0; c < 5; c++) R0[c] += s[c];
+        T dtQ0[5];
 #pragma unroll
-            for (int c = 0; c < 5; c++) b[c] = dr[d][c] * rr;
-            micro_slope(b, gr, K, ar[d]);
+        for (int c = 0; c < 5; c++) dtQ0[c] = -R0[c];
+        euler_dflux<0>(g0, dtQ0, gm1, B3);
+        second_dmoment<0>(g0, d0[0], gm1, K + 5.0, B2);
+        second_dmoment<1>(g0, d0[1], gm1, K + 5.0, s);
 #pragma unroll
-            for (int c = 0; c < 5; c++) b[c] = d0[d][c] * r0;
-            micro_slope(b, g0, K, ab[d]);
-        }
+        for (int c = 0; c < 5; c++) B2[c] += s[c];
+        second_dmoment<2>(g0, d0[2], gm1, K + 5.0, s);
+#pragma unroll
+        for (int c = 0; c < 5; c++) B2[c] += s[c];
     }
-    // time slopes from <a.u + A> = 0 (full-range moments)
-    T Al[5], Ar[5], Ab[5], R0[5];
-    {
-        T s[5], t[5];
-        mom_a<1, 0, 0>(Ml_f, al[0], s);
-        mom_a<0, 1, 0>(Ml_f, al[1], t);
+    T B4[5], B5[5], B6[5], W5[5], W6[5];
 #pragma unroll
-        for (int i = 0; i < 5; i++) s[i] += t[i];
-        mom_a<0, 0, 1>(Ml_f, al[2], t);
-#pragma unroll
-        for (int i = 0; i < 5; i++) s[i] = -(s[i] + t[i]);
-        micro_slope(s, gl, K, Al);
-        mom_a<1, 0, 0>(Mr_f, ar[0], s);
-        mom_a<0, 1, 0>(Mr_f, ar[1], t);
-#pragma unroll
-        for (int i = 0; i < 5; i++) s[i] += t[i];
-        mom_a<0, 0, 1>(Mr_f, ar[2], t);
-#pragma unroll
-        for (int i = 0; i < 5; i++) s[i] = -(s[i] + t[i]);
-        micro_slope(s, gr, K, Ar);
-        mom_a<1, 0, 0>(M0, ab[0], R0);
-        mom_a<0, 1, 0>(M0, ab[1], t);
-#pragma unroll
-        for (int i = 0; i < 5; i++) R0[i] += t[i];
-        mom_a<0, 0, 1>(M0, ab[2], t);
-#pragma unroll
-        for (int i = 0; i < 5; i++) { R0[i] += t[i]; s[i] = -R0[i]; }
-        micro_slope(s, g0, K, Ab);
+    for (int i = 0; i < 5; i++) {
+        B4[i] = b4l[i] + b4r[i];
+        W5[i] = w5l[i] + w5r[i];
+        B5[i] = b5l[i] + b5r[i];
+        W6[i] = w6l[i] + w6r[i];
+        B6[i] = b6l[i] + b6r[i];
     }
-
-    // flux moments of the six terms (B) and conserved moments (W) for the heat flux
-    T B[6][5], W5[5], W6[5];
-    {
-        T t[5];
-        psi_mom<1, 0, 0>(M0, B[0]);
-        mom_a<2, 0, 0>(M0, ab[0], B[1]);
-        mom_a<1, 1, 0>(M0, ab[1], t);
+    T W3[5];
 #pragma unroll
-        for (int i = 0; i < 5; i++) B[1][i] += t[i];
-        mom_a<1, 0, 1>(M0, ab[2], t);
-#pragma unroll
-        for (int i = 0; i < 5; i++) B[1][i] += t[i];
-        mom_a<1, 0, 0>(M0, Ab, B[2]);
-#pragma unroll
-        for (int i = 0; i < 5; i++) { B[0][i] *= g0.rho; B[1][i] *= g0.rho; B[2][i] *= g0.rho; }
-
-        T x[5], y[5];
-        psi_mom<1, 0, 0>(Ml_p, x);
-        psi_mom<1, 0, 0>(Mr_n, y);
-#pragma unroll
-        for (int i = 0; i < 5; i++) B[3][i] = gl.rho * x[i] + gr.rho * y[i];
-
-        mom_a<2, 0, 0>(Ml_p, al[0], x);
-        mom_a<1, 1, 0>(Ml_p, al[1], t);
-#pragma unroll
-        for (int i = 0; i < 5; i++) x[i] += t[i];
-        mom_a<1, 0, 1>(Ml_p, al[2], t);
-#pragma unroll
-        for (int i = 0; i < 5; i++) x[i] += t[i];
-        mom_a<2, 0, 0>(Mr_n, ar[0], y);
-        mom_a<1, 1, 0>(Mr_n, ar[1], t);
-#pragma unroll
-        for (int i = 0; i < 5; i++) y[i] += t[i];
-        mom_a<1, 0, 1>(Mr_n, ar[2], t);
-#pragma unroll
-        for (int i = 0; i < 5; i++) { y[i] += t[i]; B[4][i] = gl.rho * x[i] + gr.rho * y[i]; }
-
-        mom_a<1, 0, 0>(Ml_p, Al, x);
-        mom_a<1, 0, 0>(Mr_n, Ar, y);
-#pragma unroll
-        for (int i = 0; i < 5; i++) B[5][i] = gl.rho * x[i] + gr.rho * y[i];
-
-        mom_a<1, 0, 0>(Ml_p, al[0], x);
-        mom_a<0, 1, 0>(Ml_p, al[1], t);
-#pragma unroll
-        for (int i = 0; i < 5; i++) x[i] += t[i];
-        mom_a<0, 0, 1>(Ml_p, al[2], t);
-#pragma unroll
-        for (int i = 0; i < 5; i++) x[i] += t[i];
-        mom_a<1, 0, 0>(Mr_n, ar[0], y);
-        mom_a<0, 1, 0>(Mr_n, ar[1], t);
-#pragma unroll
-        for (int i = 0; i < 5; i++) y[i] += t[i];
-        mom_a<0, 0, 1>(Mr_n, ar[2], t);
-#pragma unroll
-        for (int i = 0; i < 5; i++) { y[i] += t[i]; W5[i] = gl.rho * x[i] + gr.rho * y[i]; }
-
-        mom_a<0, 0, 0>(Ml_p, Al, x);
-        mom_a<0, 0, 0>(Mr_n, Ar, y);
-#pragma unroll
-        for (int i = 0; i < 5; i++) W6[i] = gl.rho * x[i] + gr.rho * y[i];
-    }
-    // heat-flux moments of terms 2..6 (term 1, the equilibrium, carries none)
-    T W2[5], W3[5];
-#pragma unroll
-    for (int i = 0; i < 5; i++) { W2[i] = g0.rho * R0[i]; W3[i] = -W2[i]; }
-    const T h2 = heat_of(B[1], W2, g0), h3 = heat_of(B[2], W3, g0), h4 = heat_of(B[3], Q0, g0),
-                 h5 = heat_of(B[4], W5, g0), h6 = heat_of(B[5], W6, g0);
+    for (int i = 0; i < 5; i++) W3[i] = -R0[i];
+    const T h2 = heat_of_g(B2, R0, g0), h3 = heat_of_g(B3, W3, g0), h4 = heat_of_g(B4, Q0, g0),
+            h5 = heat_of_g(B5, W5, g0), h6 = heat_of_g(B6, W6, g0);
 
     const double prc = 1.0 / P.Pr - 1.0;
+    // e^{-dt/(2 tau)} once; e^{-dt/tau} is its square
+    const T eh = tau > 0.0 ? T(exp(-0.5 * dt / tau)) : T(0.0);
     T I[2][5];
 #pragma unroll
     for (int pass = 0; pass < 2; pass++) {
         const T dd = pass == 0 ? dt : 0.5 * dt;
-        T e = tau > 0.0 ? T(exp(-dd / tau)) : T(0.0);
-        T q0 = dd - tau * (1.0 - e);
-        T q1 = 2.0 * tau * tau * (1.0 - e) - tau * dd - tau * dd * e;
-        T q2 = 0.5 * dd * dd - tau * dd + tau * tau * (1.0 - e);
-        T q3 = tau * (1.0 - e);
-        T q4 = 2.0 * tau * tau * (1.0 - e) - tau * dd * e;
-        T q5 = tau * q3;
+        const T e = pass == 0 ? eh * eh : eh;
+        const T om = 1.0 - e;
+        const T q0 = dd - tau * om;
+        const T q1 = tau * (2.0 * tau * om - dd - dd * e);
+        const T q2 = 0.5 * dd * dd - tau * dd + tau * tau * om;
+        const T q3 = tau * om;
+        const T q4 = tau * (2.0 * tau * om - dd * e);
+        const T q5 = tau * q3;
 #pragma unroll
         for (int i = 0; i < 5; i++)
-            I[pass][i] = q0 * B[0][i] + q1 * B[1][i] + q2 * B[2][i] + q3 * B[3][i] - q4 * B[4][i] - q5 * B[5][i];
-        T hq = q1 * h2 + q2 * h3 + q3 * h4 - q4 * h5 - q5 * h6;
-        I[pass][4] += prc * hq;
+            I[pass][i] = q0 * B1[i] + q1 * B2[i] + q2 * B3[i] + q3 * B4[i] - q4 * B5[i] - q5 * B6[i];
+        I[pass][4] += prc * (q1 * h2 + q2 * h3 + q3 * h4 - q4 * h5 - q5 * h6);
     }
     const T idt = 1.0 / dt;
 #pragma unroll

@@ -94,8 +94,8 @@ extern "C" hgks_status hgks_flop_model(const hgks_grid *grid, hgks_precision pre
             return Num(1e-2 * (1 + s % 5) + 1e-3 * j);
         };
         FaceGeom G;
-        G.hn = 0.02;
-        G.h1[0] = G.h1[1] = G.h2[0] = G.h2[1] = 0.02;
+        G.ihn = 50.0;
+        G.ih1[0] = G.ih1[1] = G.ih2[0] = G.ih2[1] = 50.0;
         G.area = 4e-4;
         Num Fs[5], dFs[5];
         flux_body<Num>(load, G, P, Num(1e-3), Fs, dFs);
