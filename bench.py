@@ -22,6 +22,8 @@ import subprocess
 import sys
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -166,31 +168,64 @@ def run_ours(args, rank, world, local_rank):
     model = hg.flop_model((n, n, n))
     fp64_peak = hg.fp64_probe() if rank == 0 else None
 
-    for _ in range(args.warmup):
-        solver.step_timed(CFL)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    times = []
-    with ClockSampler(local_rank) as clk:
-        ev0.record(stream)
-        for _ in range(args.steps):
-            times.append(solver.step_timed(CFL))
-        ev1.record(stream)
+    def timed_run(sv):
+        for _ in range(args.warmup):
+            sv.step_timed(CFL)
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        times = []
+        with ClockSampler(local_rank) as clk:
+            ev0.record(stream)
+            for _ in range(args.steps):
+                times.append(sv.step_timed(CFL))
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            if world > 1:
+                dist.barrier()
+            torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        if world > 1:
+            t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, times, clk.summary()
+
+    ms, times, clocks = timed_run(solver)
     ms_per_step = ms / args.steps
     value = world * cells * args.steps / (ms * 1e-3)
+    q64 = solver.get_state()
+    s64 = solver.stats()
+
+    # the mixed-precision path on the same workload, same number of steps from
+    # the same initial field: throughput and its error against the FP64 run
+    mixed = None
+    if not args.no_mixed:
+        mx = hg.Solver((n, n, n), precision=hg.MIXED, **tgv_kwargs())
+        mx.init_tgv(MA, 1.0, 1.0)
+        ms_mx, times_mx, clocks_mx = timed_run(mx)
+        qmx = mx.get_state()
+        smx = mx.stats()
+        mx.close()
+        scale = np.abs(q64).reshape(5, -1).max(axis=1)
+        scale[1:4] = scale[1:4].max()
+        inst = float((np.abs(qmx - q64).reshape(5, -1).max(axis=1) / scale).max())
+        del qmx
+        mixed = {"value": world * cells * args.steps / (ms_mx * 1e-3), "unit": "cell-updates/s",
+                 "ms_per_step": ms_mx / args.steps,
+                 "speedup_vs_fp64": ms / ms_mx,
+                 "kernel_ms_per_step": {k: sum(t[k] for t in times_mx) / args.steps
+                                        for k in ("ghost_ms", "dt_ms", "normal_ms", "tan1_ms", "flux_ms",
+                                                  "update_ms", "other_ms")},
+                 "error_vs_fp64": {"steps": args.warmup + args.steps,
+                                   "instantaneous_rel_linf": inst,
+                                   "Ek_rel": abs(smx["Ek"] - s64["Ek"]) / abs(s64["Ek"]),
+                                   "enstrophy_rel": abs(smx["enstrophy"] - s64["enstrophy"]) / abs(s64["enstrophy"])},
+                 "clocks": clocks_mx,
+                 "gpu_launches": sum(t["launches"] for t in times_mx)}
+    del q64
 
     # end to end through the public API with host buffers: pinned H2D of the
     # state, one step, D2H of the resulting state, every step
@@ -227,7 +262,6 @@ def run_ours(args, rank, world, local_rank):
     flops_per_launch = model["flux_per_face"] * faces_per_launch
     achieved = flops_per_launch / (flux_ms / flux_launches * 1e-3) / 1e12
     peak = 1.25  # nominal dense FP64, TFLOP/s
-    clocks = clk.summary()
     line = {
         "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -248,6 +282,7 @@ def run_ours(args, rank, world, local_rank):
         "e2e": {"value": e2e_value, "unit": "cell-updates/s", "h2d_bytes_per_step": 5 * cells * 8,
                 "d2h_bytes_per_step": 5 * cells * 8, "steps": e2e_steps},
         "cpu_baseline": cpu_baseline,
+        "mixed": mixed,
         "final_stats": {"t": stats["t"], "step": stats["step"], "Ek": stats["Ek"], "enstrophy": stats["enstrophy"]},
     }
     print(json.dumps(line), flush=True)
@@ -265,6 +300,7 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")

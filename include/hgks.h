@@ -56,6 +56,10 @@ typedef enum {
 
 typedef enum { HGKS_BC_PERIODIC = 0, HGKS_BC_ISOTHERMAL_WALL = 1 } hgks_bc;
 typedef enum { HGKS_VISC_CONSTANT = 0, HGKS_VISC_POWER = 1 } hgks_visc_kind;
+/* HGKS_FP64: all arithmetic in FP64.  HGKS_MIXED: reconstruction and flux
+ * arithmetic in FP32 on deviations from FP64 centre values; FP64 for the
+ * state, the stage update, the equilibrium state Q0 (mean of the two sides
+ * plus an FP32 compatibility correction), its pressure and Euler flux. */
 typedef enum { HGKS_FP64 = 0, HGKS_MIXED = 1 } hgks_precision;
 
 /* Structured grid (Sec. 2 "orthogonal structured mesh"; Sec. 4.2 mesh map).
@@ -104,9 +108,7 @@ typedef struct {
  *   freedom K = (5 - 3 gamma)/(gamma - 1), Sec. 2).  Pr > 0 (Prandtl number,
  *   applied to the energy flux as F_E += (1/Pr - 1) q).
  *   body_force: constant acceleration (G_x, G_y, G_z) or NULL for none.
- *   precision: HGKS_FP64 (all arithmetic FP64) or HGKS_MIXED (FP32
- *   reconstruction and flux arithmetic, FP64 state, collision time and
- *   equilibrium; HGKS_ERR_INVALID_ARG until that path is built).
+ *   precision: HGKS_FP64 or HGKS_MIXED (see hgks_precision).
  *   cuda_stream: a cudaStream_t, or NULL.
  *   out: receives the handle.
  * Errors: INVALID_ARG, OOM, CUDA (no device / context failure). */

@@ -183,7 +183,8 @@ extern "C" hgks_status hgks_create(const hgks_grid *grid, double gamma, double P
     if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1 || !(grid->lx > 0) || !(grid->ly > 0) || !(grid->lz > 0))
         return set_err(nullptr, HGKS_ERR_INVALID_ARG, "grid sizes must be positive");
     if (!(gamma > 1.0) || !(Pr > 0.0)) return set_err(nullptr, HGKS_ERR_INVALID_ARG, "need gamma > 1 and Pr > 0");
-    if (precision != HGKS_FP64) return set_err(nullptr, HGKS_ERR_INVALID_ARG, "only HGKS_FP64 is available");
+    if (precision != HGKS_FP64 && precision != HGKS_MIXED)
+        return set_err(nullptr, HGKS_ERR_INVALID_ARG, "precision must be HGKS_FP64 or HGKS_MIXED");
     if (visc->kind == HGKS_VISC_POWER && !(visc->T_ref > 0.0))
         return set_err(nullptr, HGKS_ERR_INVALID_ARG, "power-law viscosity needs T_ref > 0");
     if (!(visc->mu_ref >= 0.0)) return set_err(nullptr, HGKS_ERR_INVALID_ARG, "mu_ref must be >= 0");
@@ -408,12 +409,16 @@ static void mark(StepTimer *T, int kind, int nlaunch = 1)
 static void enqueue_sweeps(hgks_t h, const double *q, bool record_wall, StepTimer *T)
 {
     const Params &P = h->P;
+    const bool mixed = h->prec == HGKS_MIXED;
     for (int d = 0; d < 3; d++) {
-        launch_normal(P, d, q, h->fq, h->ctl, h->st);
+        if (mixed) launch_sweep_mixed(P, d, q, h->fq, h->t1, h->F[d], h->ctl, h->st, 0);
+        else launch_normal(P, d, q, h->fq, h->ctl, h->st);
         mark(T, TK_NORMAL);
-        launch_tan1(P, d, h->fq, h->t1, h->ctl, h->st);
+        if (mixed) launch_sweep_mixed(P, d, q, h->fq, h->t1, h->F[d], h->ctl, h->st, 1);
+        else launch_tan1(P, d, h->fq, h->t1, h->ctl, h->st);
         mark(T, TK_TAN1);
-        launch_flux(P, d, h->t1, h->F[d], h->ctl, h->st);
+        if (mixed) launch_sweep_mixed(P, d, q, h->fq, h->t1, h->F[d], h->ctl, h->st, 2);
+        else launch_flux(P, d, h->t1, h->F[d], h->ctl, h->st);
         mark(T, TK_FLUX);
         if (d == 1 && record_wall && (P.bc_lo[1] == HGKS_BC_ISOTHERMAL_WALL || P.bc_hi[1] == HGKS_BC_ISOTHERMAL_WALL)) {
             launch_wall(P, h->F[1], h->ctl, h->grid.lx * h->grid.lz, h->st);

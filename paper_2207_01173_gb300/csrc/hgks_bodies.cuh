@@ -32,14 +32,14 @@ HGKS_HD void normal_body(Load load, Store store, double K)
         store(0 * 5 + c, lm_r);
         store(1 * 5 + c, r_l);
         // parabola through (left edge, average, right edge) of a cell, slope at its ends
-        store(2 * 5 + c, 2.0 * lm_l + 4.0 * lm_r - 6.0 * X[2]);
-        store(3 * 5 + c, -4.0 * r_l - 2.0 * r_r + 6.0 * X[3]);
+        store(2 * 5 + c, T(2.0) * lm_l + T(4.0) * lm_r - T(6.0) * X[2]);
+        store(3 * 5 + c, T(-4.0) * r_l - T(2.0) * r_r + T(6.0) * X[3]);
         // cubic through four averages, slope at the face
-        store(5 * 5 + c, (15.0 * (X[3] - X[2]) - (X[4] - X[1])) * (1.0 / 12.0));
+        store(5 * 5 + c, (T(15.0) * (X[3] - X[2]) - (X[4] - X[1])) * T(1.0 / 12.0));
     }
     // face-averaged equilibrium from the compatibility condition
     Prim<T> gl = prim_of(Ql, K), gr = prim_of(Qr, K);
-    T il = 0.5 / gl.lam, ir = 0.5 / gr.lam;
+    T il = T(0.5) / gl.lam, ir = T(0.5) / gr.lam;
     T ulp[3], vl[3], wl[3], urn[3], vr[3], wr[3];
     mom_half<3>(gl.U, gl.lam, il, true, ulp);
     mom_full<3>(gl.V, il, vl);
@@ -47,7 +47,7 @@ HGKS_HD void normal_body(Load load, Store store, double K)
     mom_half<3>(gr.U, gr.lam, ir, false, urn);
     mom_full<3>(gr.V, ir, vr);
     mom_full<3>(gr.W, ir, wr);
-    Mom<T> Ml{ ulp, vl, wl, K * il, T(0.0) }, Mr{ urn, vr, wr, K * ir, T(0.0) };
+    Mom<T> Ml{ ulp, vl, wl, T(K) * il, T(0.0) }, Mr{ urn, vr, wr, T(K) * ir, T(0.0) };
     T a[5], b[5];
     psi_mom<0, 0, 0>(Ml, a);
     psi_mom<0, 0, 0>(Mr, b);
@@ -144,29 +144,29 @@ HGKS_HD void flux_body(Load load, const FaceGeom &G, const Params &P, T dt, T Fs
             T dl[3][5], dr[3][5], d0[3][5];
 #pragma unroll
             for (int c = 0; c < 5; c++) {
-                dl[0][c] = gv[n][10 + c] * G.ihn;
-                dr[0][c] = gv[n][15 + c] * G.ihn;
-                d0[0][c] = gv[n][20 + c] * G.ihn;
-                dl[1][c] = gd1[n][c] * ih1;
-                dr[1][c] = gd1[n][5 + c] * ih1;
-                d0[1][c] = gd1[n][10 + c] * ih1;
-                dl[2][c] = gd2[n][c] * ih2;
-                dr[2][c] = gd2[n][5 + c] * ih2;
-                d0[2][c] = gd2[n][10 + c] * ih2;
+                dl[0][c] = gv[n][10 + c] * T(G.ihn);
+                dr[0][c] = gv[n][15 + c] * T(G.ihn);
+                d0[0][c] = gv[n][20 + c] * T(G.ihn);
+                dl[1][c] = gd1[n][c] * T(ih1);
+                dr[1][c] = gd1[n][5 + c] * T(ih1);
+                d0[1][c] = gd1[n][10 + c] * T(ih1);
+                dl[2][c] = gd2[n][c] * T(ih2);
+                dr[2][c] = gd2[n][5 + c] * T(ih2);
+                d0[2][c] = gd2[n][10 + c] * T(ih2);
             }
             T Fn[5], dFn[5];
             gks_point_flux<T>(&gv[n][0], &gv[n][5], dl, dr, d0, P, dt, Fn, dFn);
 #pragma unroll
             for (int c = 0; c < 5; c++) {
-                Fs[c] += 0.25 * Fn[c];
-                dFs[c] += 0.25 * dFn[c];
+                Fs[c] += T(0.25) * Fn[c];
+                dFs[c] += T(0.25) * dFn[c];
             }
         }
     }
 #pragma unroll
     for (int c = 0; c < 5; c++) {
-        Fs[c] = Fs[c] * G.area;
-        dFs[c] = dFs[c] * G.area;
+        Fs[c] = Fs[c] * T(G.area);
+        dFs[c] = dFs[c] * T(G.area);
     }
 }
 

@@ -92,15 +92,16 @@ HGKS_HD void weno_prep(const T X[5], WenoPrep<T> &W)
     // candidate slopes and curvatures from the first differences of the averages
     const T d1 = X[1] - X[0], d2 = X[2] - X[1], d3 = X[3] - X[2], d4 = X[4] - X[3];
     W.x0 = X[2];
-    W.c2[0] = 0.5 * (d2 - d1);
-    W.c1[0] = 1.5 * d2 - 0.5 * d1;
-    W.c2[1] = 0.5 * (d3 - d2);
-    W.c1[1] = 0.5 * (d3 + d2);
-    W.c2[2] = 0.5 * (d4 - d3);
-    W.c1[2] = 1.5 * d3 - 0.5 * d4;
+    const T h = T(0.5), t3 = T(1.5);
+    W.c2[0] = h * (d2 - d1);
+    W.c1[0] = t3 * d2 - h * d1;
+    W.c2[1] = h * (d3 - d2);
+    W.c1[1] = h * (d3 + d2);
+    W.c2[2] = h * (d4 - d3);
+    W.c1[2] = t3 * d3 - h * d4;
     T b[3];
 #pragma unroll
-    for (int k = 0; k < 3; k++) b[k] = W.c1[k] * W.c1[k] + (13.0 / 3.0) * W.c2[k] * W.c2[k] + WENO_EPS;
+    for (int k = 0; k < 3; k++) b[k] = W.c1[k] * W.c1[k] + T(13.0 / 3.0) * W.c2[k] * W.c2[k] + T(WENO_EPS);
     T tau5 = fabs(b[0] - b[2]);
     W.cw[0] = (b[0] + tau5) * (b[1] * b[2]);
     W.cw[1] = (b[1] + tau5) * (b[0] * b[2]);
@@ -112,28 +113,30 @@ HGKS_HD void weno_prep(const T X[5], WenoPrep<T> &W)
 template <typename T>
 HGKS_HD void weno_gauss_pair(const WenoPrep<T> &W, T &vm, T &vp)
 {
-    const T e0 = HGKS_DGL * W.cw[0], e2 = HGKS_DGR * W.cw[2], f0 = HGKS_DGR * W.cw[0], f2 = HGKS_DGL * W.cw[2];
-    const T a1 = HGKS_DGC * W.cw[1];
+    const T dgl = T(HGKS_DGL), dgr = T(HGKS_DGR);
+    const T e0 = dgl * W.cw[0], e2 = dgr * W.cw[2], f0 = dgr * W.cw[0], f2 = dgl * W.cw[2];
+    const T a1 = T(HGKS_DGC) * W.cw[1];
     const T dp = e0 + a1 + e2, dm = f0 + a1 + f2;  // plus: (DGL, DGC, DGR), minus: mirrored
     const T np = e0 * W.c1[0] + a1 * W.c1[1] + e2 * W.c1[2];
     const T nm = f0 * W.c1[0] + a1 * W.c1[1] + f2 * W.c1[2];
-    const T r = 1.0 / (dp * dm);
-    vp = W.x0 + HGKS_GAUSS * (np * dm * r);
-    vm = W.x0 - HGKS_GAUSS * (nm * dp * r);
+    const T r = T(1.0) / (dp * dm);
+    vp = W.x0 + T(HGKS_GAUSS) * (np * dm * r);
+    vm = W.x0 - T(HGKS_GAUSS) * (nm * dp * r);
 }
 
 // both cell edges (-1/2: vl, +1/2: vr) from one reciprocal
 template <typename T>
 HGKS_HD void weno_edge_pair(const WenoPrep<T> &W, T &vl, T &vr)
 {
-    const T a1 = 0.6 * W.cw[1];
-    const T r0 = 0.1 * W.cw[0], r2 = 0.3 * W.cw[2];  // right edge weights
-    const T l0 = 0.3 * W.cw[0], l2 = 0.1 * W.cw[2];  // left edge weights
-    const T p0 = W.x0 + W.c2[0] * (1.0 / 6.0), p1 = W.x0 + W.c2[1] * (1.0 / 6.0), p2 = W.x0 + W.c2[2] * (1.0 / 6.0);
-    const T nr = r0 * (p0 + 0.5 * W.c1[0]) + a1 * (p1 + 0.5 * W.c1[1]) + r2 * (p2 + 0.5 * W.c1[2]);
-    const T nl = l0 * (p0 - 0.5 * W.c1[0]) + a1 * (p1 - 0.5 * W.c1[1]) + l2 * (p2 - 0.5 * W.c1[2]);
+    const T c01 = T(0.1), c03 = T(0.3), c06 = T(0.6), c16 = T(1.0 / 6.0), h = T(0.5);
+    const T a1 = c06 * W.cw[1];
+    const T r0 = c01 * W.cw[0], r2 = c03 * W.cw[2];  // right edge weights
+    const T l0 = c03 * W.cw[0], l2 = c01 * W.cw[2];  // left edge weights
+    const T p0 = W.x0 + W.c2[0] * c16, p1 = W.x0 + W.c2[1] * c16, p2 = W.x0 + W.c2[2] * c16;
+    const T nr = r0 * (p0 + h * W.c1[0]) + a1 * (p1 + h * W.c1[1]) + r2 * (p2 + h * W.c1[2]);
+    const T nl = l0 * (p0 - h * W.c1[0]) + a1 * (p1 - h * W.c1[1]) + l2 * (p2 - h * W.c1[2]);
     const T dr = r0 + a1 + r2, dl = l0 + a1 + l2;
-    const T r = 1.0 / (dr * dl);
+    const T r = T(1.0) / (dr * dl);
     vr = nr * dl * r;
     vl = nl * dr * r;
 }
@@ -147,16 +150,16 @@ HGKS_HD void weno_edge_pair(const WenoPrep<T> &W, T &vl, T &vr)
 template <typename T>
 HGKS_HD void quartic_value_pair(const T X[5], T &vm, T &vp)
 {
-    const T e = (-1.0 / 4320.0) * (X[0] + X[4]) + (1.0 / 1080.0) * (X[1] + X[3]) + (719.0 / 720.0) * X[2];
-    const T o = HGKS_SQ3 * ((7.0 / 432.0) * (X[0] - X[4]) + (25.0 / 216.0) * (X[3] - X[1]));
+    const T e = T(-1.0 / 4320.0) * (X[0] + X[4]) + T(1.0 / 1080.0) * (X[1] + X[3]) + T(719.0 / 720.0) * X[2];
+    const T o = T(HGKS_SQ3) * (T(7.0 / 432.0) * (X[0] - X[4]) + T(25.0 / 216.0) * (X[3] - X[1]));
     vm = e - o;
     vp = e + o;
 }
 template <typename T>
 HGKS_HD void quartic_deriv_pair(const T X[5], T &dm, T &dp)
 {
-    const T c = (1.0 / 12.0) * (X[0] - X[4]) + (2.0 / 3.0) * (X[3] - X[1]);
-    const T s = HGKS_SQ3 * ((1.0 / 54.0) * (X[0] + X[4]) - (13.0 / 54.0) * (X[1] + X[3]) + (24.0 / 54.0) * X[2]);
+    const T c = T(1.0 / 12.0) * (X[0] - X[4]) + T(2.0 / 3.0) * (X[3] - X[1]);
+    const T s = T(HGKS_SQ3) * (T(1.0 / 54.0) * (X[0] + X[4]) - T(13.0 / 54.0) * (X[1] + X[3]) + T(24.0 / 54.0) * X[2]);
     dm = c + s;
     dp = c - s;
 }
@@ -173,13 +176,13 @@ template <typename T>
 HGKS_HD Prim<T> prim_of(const T Q[5], double K)
 {
     Prim<T> g;
-    T ir = 1.0 / Q[0];
+    T ir = T(1.0) / Q[0];
     g.rho = Q[0];
     g.U = Q[1] * ir;
     g.V = Q[2] * ir;
     g.W = Q[3] * ir;
-    T eint = Q[4] - 0.5 * Q[0] * (g.U * g.U + g.V * g.V + g.W * g.W);
-    g.lam = (K + 3.0) * Q[0] / (4.0 * eint);
+    T eint = Q[4] - T(0.5) * Q[0] * (g.U * g.U + g.V * g.V + g.W * g.W);
+    g.lam = T(K + 3.0) * Q[0] / (T(4.0) * eint);
     return g;
 }
 
@@ -187,28 +190,28 @@ HGKS_HD Prim<T> prim_of(const T Q[5], double K)
 template <int N, typename T>
 HGKS_HD void mom_full(T U, T i2l, T *m)
 {
-    m[0] = 1.0;
+    m[0] = T(1.0);
     m[1] = U;
 #pragma unroll
-    for (int n = 0; n + 2 < N; n++) m[n + 2] = U * m[n + 1] + (double)(n + 1) * i2l * m[n];
+    for (int n = 0; n + 2 < N; n++) m[n + 2] = U * m[n + 1] + T(n + 1) * i2l * m[n];
 }
 
 // half-range moments over u > 0 (pos) or u < 0
 template <int N, typename T>
 HGKS_HD void mom_half(T U, T lam, T i2l, bool pos, T *m)
 {
-    const double inv_2sqrtpi = 0.28209479177387814347; // 1 / (2 sqrt(pi))
+    const T inv_2sqrtpi = T(0.28209479177387814347); // 1 / (2 sqrt(pi))
     T sl = sqrt(lam);
     T e = exp(-lam * U * U) * inv_2sqrtpi / sl;
     if (pos) {
-        m[0] = 0.5 * erfc(-sl * U);
+        m[0] = T(0.5) * erfc(-sl * U);
         m[1] = U * m[0] + e;
     } else {
-        m[0] = 0.5 * erfc(sl * U);
+        m[0] = T(0.5) * erfc(sl * U);
         m[1] = U * m[0] - e;
     }
 #pragma unroll
-    for (int n = 0; n + 2 < N; n++) m[n + 2] = U * m[n + 1] + (double)(n + 1) * i2l * m[n];
+    for (int n = 0; n + 2 < N; n++) m[n + 2] = U * m[n + 1] + T(n + 1) * i2l * m[n];
 }
 
 // moments of one state: u (range specific), v, w (full), xi
@@ -229,14 +232,14 @@ HGKS_HD void psi_mom(const Mom<T> &m, T o[5])
     o[1] = m.u[A + 1] * m.v[B] * m.w[C];
     o[2] = m.u[A] * m.v[B + 1] * m.w[C];
     o[3] = m.u[A] * m.v[B] * m.w[C + 1];
-    o[4] = 0.5 * (m.u[A + 2] * m.v[B] * m.w[C] + m.u[A] * m.v[B + 2] * m.w[C] + m.u[A] * m.v[B] * m.w[C + 2]
-                  + uvw * m.xi1);
+    o[4] = T(0.5) * (m.u[A + 2] * m.v[B] * m.w[C] + m.u[A] * m.v[B + 2] * m.w[C] + m.u[A] * m.v[B] * m.w[C + 2]
+                     + uvw * m.xi1);
 }
 
 template <typename T>
 HGKS_HD T viscosity(const Params &P, T Tm)
 {
-    return P.visc_kind == 1 ? P.mu_ref * pow(Tm / P.T_ref, P.omega) : T(P.mu_ref);
+    return P.visc_kind == 1 ? T(P.mu_ref) * pow(Tm * T(1.0 / P.T_ref), T(P.omega)) : T(P.mu_ref);
 }
 
 // ---------------------------------------------------------------------------
@@ -263,16 +266,16 @@ HGKS_HD Gas<T> gas_of(const T Q[5], double gm1)
 {
     Gas<T> g;
     g.rho = Q[0];
-    g.ir = 1.0 / Q[0];
+    g.ir = T(1.0) / Q[0];
     g.U[0] = Q[1] * g.ir;
     g.U[1] = Q[2] * g.ir;
     g.U[2] = Q[3] * g.ir;
     g.uu = g.U[0] * g.U[0] + g.U[1] * g.U[1] + g.U[2] * g.U[2];
     g.E = Q[4];
-    g.p = gm1 * (Q[4] - 0.5 * Q[0] * g.uu);
+    g.p = T(gm1) * (Q[4] - T(0.5) * Q[0] * g.uu);
     g.Tm = g.p * g.ir;
-    g.tl = 1.0 / g.Tm;
-    g.lam = 0.5 * g.tl;
+    g.tl = T(1.0) / g.Tm;
+    g.lam = T(0.5) * g.tl;
     return g;
 }
 
@@ -280,7 +283,7 @@ HGKS_HD Gas<T> gas_of(const T Q[5], double gm1)
 template <int D, typename T>
 HGKS_HD void euler_dflux(const Gas<T> &g, const T dQ[5], double gm1, T o[5])
 {
-    const T dp = gm1 * (dQ[4] - (g.U[0] * dQ[1] + g.U[1] * dQ[2] + g.U[2] * dQ[3]) + 0.5 * g.uu * dQ[0]);
+    const T dp = T(gm1) * (dQ[4] - (g.U[0] * dQ[1] + g.U[1] * dQ[2] + g.U[2] * dQ[3]) + T(0.5) * g.uu * dQ[0]);
     const T dUd = (dQ[1 + D] - g.U[D] * dQ[0]) * g.ir;
     o[0] = dQ[1 + D];
 #pragma unroll
@@ -302,7 +305,7 @@ HGKS_HD void second_dmoment(const Gas<T> &g, const T dQ[5], double gm1, double K
     T dU[3];
 #pragma unroll
     for (int k = 0; k < 3; k++) dU[k] = (dQ[1 + k] - g.U[k] * drho) * g.ir;
-    const T dp = gm1 * (dQ[4] - (g.U[0] * dQ[1] + g.U[1] * dQ[2] + g.U[2] * dQ[3]) + 0.5 * g.uu * drho);
+    const T dp = T(gm1) * (dQ[4] - (g.U[0] * dQ[1] + g.U[1] * dQ[2] + g.U[2] * dQ[3]) + T(0.5) * g.uu * drho);
     const T Un = g.U[0], Ud = g.U[D], dUn = dU[0], dUd = dU[D];
     const T dUnUd = dUn * Ud + Un * dUd;  // d(Un Ud)
     const T UnUd = Un * Ud;
@@ -316,10 +319,11 @@ HGKS_HD void second_dmoment(const Gas<T> &g, const T dQ[5], double gm1, double K
         if (k == D) v += dp * Un + g.p * dUn;
         o[1 + k] = v;
     }
-    o[4] = dUnUd * (g.E + 2.0 * g.p) + UnUd * (dQ[4] + 2.0 * dp);
+    o[4] = dUnUd * (g.E + T(2.0) * g.p) + UnUd * (dQ[4] + T(2.0) * dp);
     if (D == 0) {
         const T UdU = g.U[0] * dU[0] + g.U[1] * dU[1] + g.U[2] * dU[2];
-        o[4] += 0.5 * (dp * (g.uu + Kp5 * g.Tm) + g.p * (2.0 * UdU + Kp5 * (dp - g.Tm * drho) * g.ir));
+        const T kp5 = T(Kp5);
+        o[4] += T(0.5) * (dp * (g.uu + kp5 * g.Tm) + g.p * (T(2.0) * UdU + kp5 * (dp - g.Tm * drho) * g.ir));
     }
 }
 
@@ -327,8 +331,8 @@ template <typename T>
 HGKS_HD T heat_of_g(const T B[5], const T W[5], const Gas<T> &g0)
 {
     const T U0 = g0.U[0], V0 = g0.U[1], W0 = g0.U[2], uu = g0.uu;
-    return B[4] - U0 * B[1] - V0 * B[2] - W0 * B[3] + 0.5 * uu * B[0]
-         - U0 * W[4] + U0 * U0 * W[1] + U0 * V0 * W[2] + U0 * W0 * W[3] - 0.5 * U0 * uu * W[0];
+    return B[4] - U0 * B[1] - V0 * B[2] - W0 * B[3] + T(0.5) * uu * B[0]
+         - U0 * W[4] + U0 * U0 * W[1] + U0 * V0 * W[2] + U0 * W0 * W[3] - T(0.5) * U0 * uu * W[0];
 }
 
 // ---------------------------------------------------------------------------
@@ -359,52 +363,52 @@ template <typename T>
 HGKS_HD void half_side_setup(const T Q[5], double gm1, double K, bool pos, HalfSide<T> &h)
 {
     h.rho = Q[0];
-    h.ir = 1.0 / Q[0];
+    h.ir = T(1.0) / Q[0];
     h.U[0] = Q[1] * h.ir;
     h.U[1] = Q[2] * h.ir;
     h.U[2] = Q[3] * h.ir;
     h.uu = h.U[0] * h.U[0] + h.U[1] * h.U[1] + h.U[2] * h.U[2];
     h.E = Q[4];
-    h.p = gm1 * (Q[4] - 0.5 * Q[0] * h.uu);
+    h.p = T(gm1) * (Q[4] - T(0.5) * Q[0] * h.uu);
     h.Tm = h.p * h.ir;
-    const double sg = pos ? 1.0 : -1.0;
-    const double inv_sqrt2pi = 0.39894228040143267794;  // 1/sqrt(2 pi)
-    const T iTm = 1.0 / h.Tm;
-    const T isq = sqrt(iTm);                              // 1/sqrt(T)
+    const T sg = T(pos ? 1.0 : -1.0);
+    const T inv_sqrt2pi = T(0.39894228040143267794);  // 1/sqrt(2 pi)
+    const T iTm = T(1.0) / h.Tm;
+    const T isq = sqrt(iTm);                            // 1/sqrt(T)
     const T U = h.U[0];
-    const T phi0 = exp(-0.5 * U * U * iTm) * (inv_sqrt2pi * isq);
-    h.u[0] = 0.5 * erfc((-sg * 0.70710678118654752440) * U * isq);
+    const T phi0 = exp(T(-0.5) * U * U * iTm) * (inv_sqrt2pi * isq);
+    h.u[0] = T(0.5) * erfc(T(pos ? -0.70710678118654752440 : 0.70710678118654752440) * U * isq);
     h.u[1] = U * h.u[0] + sg * h.Tm * phi0;
 #pragma unroll
-    for (int n = 0; n < 3; n++) h.u[n + 2] = U * h.u[n + 1] + (double)(n + 1) * h.Tm * h.u[n];
+    for (int n = 0; n < 3; n++) h.u[n + 2] = U * h.u[n + 1] + T(n + 1) * h.Tm * h.u[n];
     h.uU[0] = sg * phi0;
-    h.uT[0] = (-0.5 * sg) * U * iTm * phi0;
+    h.uT[0] = T(pos ? -0.5 : 0.5) * U * iTm * phi0;
     h.uU[1] = h.u[0];
-    h.uT[1] = (0.5 * sg) * phi0;
+    h.uT[1] = T(pos ? 0.5 : -0.5) * phi0;
 #pragma unroll
     for (int n = 2; n < 5; n++) {
-        h.uU[n] = (double)n * h.u[n - 1];
-        h.uT[n] = (0.5 * n * (n - 1)) * h.u[n - 2];
+        h.uU[n] = T(n) * h.u[n - 1];
+        h.uT[n] = T(0.5 * n * (n - 1)) * h.u[n - 2];
     }
     mom_full<4>(h.U[1], h.Tm, h.v);
     mom_full<4>(h.U[2], h.Tm, h.w);
-    h.vV[0] = 0.0;
-    h.wW[0] = 0.0;
-    h.vT[0] = 0.0;
-    h.wT[0] = 0.0;
-    h.vT[1] = 0.0;
-    h.wT[1] = 0.0;
+    h.vV[0] = T(0.0);
+    h.wW[0] = T(0.0);
+    h.vT[0] = T(0.0);
+    h.wT[0] = T(0.0);
+    h.vT[1] = T(0.0);
+    h.wT[1] = T(0.0);
 #pragma unroll
     for (int n = 1; n < 4; n++) {
-        h.vV[n] = (double)n * h.v[n - 1];
-        h.wW[n] = (double)n * h.w[n - 1];
+        h.vV[n] = T(n) * h.v[n - 1];
+        h.wW[n] = T(n) * h.w[n - 1];
     }
 #pragma unroll
     for (int n = 2; n < 4; n++) {
-        h.vT[n] = (0.5 * n * (n - 1)) * h.v[n - 2];
-        h.wT[n] = (0.5 * n * (n - 1)) * h.w[n - 2];
+        h.vT[n] = T(0.5 * n * (n - 1)) * h.v[n - 2];
+        h.wT[n] = T(0.5 * n * (n - 1)) * h.w[n - 2];
     }
-    h.xi1 = K * h.Tm;
+    h.xi1 = T(K) * h.Tm;
 }
 
 // value of Phi_m = rho <u^E v^J w^L psi>_sigma
@@ -417,7 +421,7 @@ HGKS_HD void half_phi(const HalfSide<T> &h, T o[5])
     o[1] = h.rho * (h.u[E + 1] * bc);
     o[2] = h.rho * (h.u[E] * h.v[J + 1] * h.w[L]);
     o[3] = h.rho * (h.u[E] * h.v[J] * h.w[L + 1]);
-    o[4] = (0.5 * h.rho) * (h.u[E + 2] * bc + h.u[E] * (h.v[J + 2] * h.w[L] + h.v[J] * h.w[L + 2]) + h.xi1 * abc);
+    o[4] = (T(0.5) * h.rho) * (h.u[E + 2] * bc + h.u[E] * (h.v[J + 2] * h.w[L] + h.v[J] * h.w[L + 2]) + h.xi1 * abc);
 }
 
 // changes of the primitives and of the 1-D moments along a change dQ of the
@@ -433,7 +437,7 @@ HGKS_HD void half_delta(const HalfSide<T> &h, const T dQ[5], double gm1, double 
     const T dU = (dQ[1] - h.U[0] * dQ[0]) * h.ir;
     const T dV = (dQ[2] - h.U[1] * dQ[0]) * h.ir;
     const T dW = (dQ[3] - h.U[2] * dQ[0]) * h.ir;
-    const T dp = gm1 * (dQ[4] - (h.U[0] * dQ[1] + h.U[1] * dQ[2] + h.U[2] * dQ[3]) + 0.5 * h.uu * dQ[0]);
+    const T dp = T(gm1) * (dQ[4] - (h.U[0] * dQ[1] + h.U[1] * dQ[2] + h.U[2] * dQ[3]) + T(0.5) * h.uu * dQ[0]);
     const T dT = (dp - h.Tm * dQ[0]) * h.ir;
     d.rho = dQ[0];
 #pragma unroll
@@ -443,7 +447,7 @@ HGKS_HD void half_delta(const HalfSide<T> &h, const T dQ[5], double gm1, double 
         d.dv[n] = h.vV[n] * dV + h.vT[n] * dT;
         d.dw[n] = h.wW[n] * dW + h.wT[n] * dT;
     }
-    d.dxi1 = K * dT;
+    d.dxi1 = T(K) * dT;
 }
 
 // directional derivative of Phi_m along the change d (product rule)
@@ -465,7 +469,7 @@ HGKS_HD void half_dphi(const HalfSide<T> &h, const HalfDelta<T> &d, T o[5])
     const T p5 = prod(h.u[E], d.du[E], h.v[J + 2], d.dv[J + 2], h.w[L], d.dw[L], v5);
     const T p6 = prod(h.u[E], d.du[E], h.v[J], d.dv[J], h.w[L + 2], d.dw[L + 2], v6);
     // xi^2 term: D(rho xi1 abc) = xi1 D(rho abc) + rho abc dxi1
-    o[4] = 0.5 * (p4 + p5 + p6 + h.xi1 * o[0] + h.rho * v0 * d.dxi1);
+    o[4] = T(0.5) * (p4 + p5 + p6 + h.xi1 * o[0] + h.rho * v0 * d.dxi1);
 }
 
 // time change of the conserved variables of an Euler state: d_t Q = -sum_d DF_d(Q)[d_d Q]
@@ -595,31 +599,31 @@ __host__ __device__ __noinline__ void gks_point_flux(const T Ql[5], const T Qr[5
     const T h2 = heat_of_g(B2, R0, g0), h3 = heat_of_g(B3, W3, g0), h4 = heat_of_g(B4, Q0, g0),
             h5 = heat_of_g(B5, W5, g0), h6 = heat_of_g(B6, W6, g0);
 
-    const double prc = 1.0 / P.Pr - 1.0;
+    const T prc = T(1.0 / P.Pr - 1.0);
     // e^{-dt/(2 tau)} once; e^{-dt/tau} is its square
-    const T eh = tau > 0.0 ? T(exp(-0.5 * dt / tau)) : T(0.0);
+    const T eh = tau > T(0.0) ? T(exp(T(-0.5) * dt / tau)) : T(0.0);
     T I[2][5];
 #pragma unroll
     for (int pass = 0; pass < 2; pass++) {
-        const T dd = pass == 0 ? dt : 0.5 * dt;
+        const T dd = pass == 0 ? dt : T(0.5) * dt;
         const T e = pass == 0 ? eh * eh : eh;
-        const T om = 1.0 - e;
+        const T om = T(1.0) - e;
         const T q0 = dd - tau * om;
-        const T q1 = tau * (2.0 * tau * om - dd - dd * e);
-        const T q2 = 0.5 * dd * dd - tau * dd + tau * tau * om;
+        const T q1 = tau * (T(2.0) * tau * om - dd - dd * e);
+        const T q2 = T(0.5) * dd * dd - tau * dd + tau * tau * om;
         const T q3 = tau * om;
-        const T q4 = tau * (2.0 * tau * om - dd * e);
+        const T q4 = tau * (T(2.0) * tau * om - dd * e);
         const T q5 = tau * q3;
 #pragma unroll
         for (int i = 0; i < 5; i++)
             I[pass][i] = q0 * B1[i] + q1 * B2[i] + q2 * B3[i] + q3 * B4[i] - q4 * B5[i] - q5 * B6[i];
         I[pass][4] += prc * (q1 * h2 + q2 * h3 + q3 * h4 - q4 * h5 - q5 * h6);
     }
-    const T idt = 1.0 / dt;
+    const T idt = T(1.0) / dt;
 #pragma unroll
     for (int i = 0; i < 5; i++) {
-        Fn[i] = (4.0 * I[1][i] - I[0][i]) * idt;
-        dFn[i] = 4.0 * (I[0][i] - 2.0 * I[1][i]) * idt * idt;
+        Fn[i] = (T(4.0) * I[1][i] - I[0][i]) * idt;
+        dFn[i] = T(4.0) * (I[0][i] - T(2.0) * I[1][i]) * idt * idt;
     }
 }
 

@@ -35,6 +35,10 @@ void launch_normal(const Params &P, int d, const double *q, double *fq, const Ct
 void launch_tan1(const Params &P, int d, const double *fq, double *t1, const Ctl *ctl, cudaStream_t st);
 void launch_flux(const Params &P, int d, const double *t1, double *F, const Ctl *ctl, cudaStream_t st);
 void launch_wall(const Params &P, const double *Fy, Ctl *ctl, double lxlz, cudaStream_t st);
+// mixed-precision sweep passes (which: 0 normal, 1 first tangential, 2 flux),
+// using the same fq / t1 buffers as the FP64 passes
+void launch_sweep_mixed(const Params &P, int d, const double *q, double *fq, double *t1, double *F, const Ctl *ctl,
+                        cudaStream_t st, int which);
 // stage 1: qs = q + dt/2 L + dt^2/8 dL, r = q + dt L + dt^2/6 dL;  stage 2: qn = r + dt^2/3 dL
 void launch_update(const Params &P, int stage, const double *q, const double *const F[3], double *out_a,
                    double *out_b, Ctl *ctl, cudaStream_t st);

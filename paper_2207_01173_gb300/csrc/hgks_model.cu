@@ -39,7 +39,7 @@ inline Num fabs(Num a) { return Num(std::fabs(a.v)); }
 inline Num sqrt(Num a) { cur->special += 1; return Num(std::sqrt(a.v)); }
 inline Num exp(Num a) { cur->special += 1; return Num(std::exp(a.v)); }
 inline Num erfc(Num a) { cur->special += 1; return Num(std::erfc(a.v)); }
-inline Num pow(Num a, double e) { cur->special += 1; return Num(std::pow(a.v, e)); }
+inline Num pow(Num a, Num e) { cur->special += 1; return Num(std::pow(a.v, e.v)); }
 
 }  // namespace hgks_count
 

@@ -1,0 +1,102 @@
+"""The mixed-precision path (HGKS_MIXED) against the FP64 oracle.
+
+Stated error of the mixed path, measured on a GB300 (instantaneous: relative
+L-inf of the conservative variables, momenta sharing one normaliser;
+statistical: relative difference of the volume-averaged diagnostics):
+  * TGV 32^3, 10 steps: instantaneous 1.6e-8, E_k / enstrophy 5e-10;
+  * TGV 64^3, 200 steps against the FP64 GPU path: instantaneous 2.9e-8,
+    E_k 4e-10, enstrophy 1.1e-9;
+  * noisy channel 16 x 24 x 12, 10 steps: instantaneous 1.4e-6 (10 % random
+    velocity noise: large jumps take the direct FP32 compatibility branch).
+The bounds below leave a factor of about five.  Properties that hold
+exactly in both precisions (conservation through telescoping FP64 face
+fluxes, free-stream preservation) are checked exactly.
+"""
+import numpy as np
+import pytest
+
+from tests.test_gpu_parity import TGV_KW, channel_kw, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hg():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2207_01173_gb300 import hgks
+    return hgks
+
+
+def test_mixed_tgv32_against_oracle(hg, oracle):
+    n = (32, 32, 32)
+    g = hg.Solver(n, precision=hg.MIXED, **TGV_KW)
+    c = oracle.RefSolver(n, **TGV_KW)
+    g.init_tgv(0.1, 1.0, 1.0)
+    c.init_tgv(0.1, 1.0, 1.0)
+    g.step(10, 0.5)
+    c.step(10, 0.5)
+    err = rel_err(g.get_state(), c.get_state())
+    assert err.max() < 1e-7, err
+    sg, sc = g.stats(), c.stats()
+    for k in ("Ek", "enstrophy", "eps_com"):
+        assert sg[k] == pytest.approx(sc[k], rel=3e-9), k
+    assert sg["mass"] == pytest.approx(sc["mass"], rel=1e-13)
+    assert sg["energy"] == pytest.approx(sc["energy"], rel=1e-13)
+
+
+def test_mixed_channel_against_oracle(hg, oracle):
+    n = (16, 24, 12)
+    g = hg.Solver(n, precision=hg.MIXED, **channel_kw())
+    c = oracle.RefSolver(n, **channel_kw())
+    g.init_channel(0.5, 0.1, 2800)
+    c.init_channel(0.5, 0.1, 2800)
+    g.step(10, 0.5)
+    c.step(10, 0.5)
+    err = rel_err(g.get_state(), c.get_state())
+    assert err.max() < 1e-5, err
+
+
+def test_mixed_conserves_to_roundoff(hg):
+    """Face fluxes are single FP64 values shared by both neighbours, so the
+    periodic totals telescope exactly as in FP64."""
+    from tests.inputs import smooth_state
+    n = (20, 18, 16)
+    g = hg.Solver(n, precision=hg.MIXED, **TGV_KW)
+    q = smooth_state(n, 21)
+    g.set_state(q)
+    a = g.stats()
+    g.step(10, 0.5)
+    b = g.stats()
+    assert abs(b["mass"] - a["mass"]) <= 1e-13 * abs(a["mass"])
+    assert abs(b["energy"] - a["energy"]) <= 1e-13 * abs(a["energy"])
+    for i in range(3):
+        assert abs(b["mom"][i] - a["mom"][i]) <= 1e-13 * abs(a["mass"])
+
+
+def test_mixed_free_stream_bitwise(hg):
+    n = (7, 5, 6)
+    g = hg.Solver(n, lengths=(1.0, 2.0, 1.5), visc=(0, 1e-3, 1.0, 0.0), precision=hg.MIXED)
+    q = np.empty((5, 6, 5, 7))
+    for c, v in enumerate((1.3, 0.52, -0.325, 0.13, 2.4)):
+        q[c] = v
+    g.set_state(q)
+    g.step(5, 0.5)
+    assert np.array_equal(g.get_state(), q)
+
+
+def test_mixed_tracks_fp64_over_200_steps(hg):
+    """Statistical error on a longer run: E_k and enstrophy histories of the
+    mixed path follow the FP64 path within 5e-9 relative over 200 steps of
+    TGV 64^3, the instantaneous state within 2e-7."""
+    n = (64, 64, 64)
+    gs = [hg.Solver(n, precision=p, **TGV_KW) for p in (hg.FP64, hg.MIXED)]
+    for g in gs:
+        g.init_tgv(0.1, 1.0, 1.0)
+    for _ in range(4):
+        for g in gs:
+            g.step(50, 0.5)
+        s0, s1 = gs[0].stats(), gs[1].stats()
+        assert s1["Ek"] == pytest.approx(s0["Ek"], rel=5e-9)
+        assert s1["enstrophy"] == pytest.approx(s0["enstrophy"], rel=5e-9)
+    assert rel_err(gs[1].get_state(), gs[0].get_state()).max() < 2e-7
