@@ -225,6 +225,59 @@ hgks_status hgks_flop_model(const hgks_grid *grid, hgks_precision precision, hgk
 hgks_status hgks_cfl_dt_noalloc(const hgks_grid *grid, double gamma, double cfl, const double *d_q,
                                 double *d_dt, void *cuda_stream);
 
+/* ---- batches: many problems advanced together -------------------------
+ * The paper advances one problem at a time; batching has no counterpart
+ * there.  Every problem of a batch takes exactly the step of hgks_step (the
+ * two-stage step of Eq. "two-stage" with the fluxes of Eq. "flux"), with the
+ * same arithmetic, so a batch reproduces its problems stepped one by one bit
+ * for bit.
+ * A batch groups n solver handles (any grids, gas parameters and precisions,
+ * all created on one CUDA stream) so that each pass of a step runs as one
+ * persistent kernel over a tile work-list spanning all of them, and the whole
+ * step is one captured CUDA graph replayed on the batch's own stream.
+ * Ownership: the batch borrows the handles and their device buffers; destroy
+ * the batch before any of its handles.  Between batch calls the handles stay
+ * usable on their own (init, state copies, stats, hgks_step).
+ * Each problem keeps its own time step, step counter and bad-state flag: a
+ * problem whose stage produces a non-finite or non-positive state stops at
+ * its last completed step for the rest of the call while the others advance,
+ * and the call returns HGKS_ERR_NONFINITE naming it in
+ * hgks_batch_last_error; its flag is cleared on return. */
+typedef struct hgks_batch_s *hgks_batch_t;
+typedef struct {
+    int problems;          /* handles in the batch */
+    int tile_sweep;        /* interface positions per tile of the sweep passes */
+    int tile_cells;        /* cells per tile of the cell passes */
+    int launches_per_step; /* kernel nodes of the per-step graph */
+    long long tiles;       /* tiles over all passes */
+    double last_ms;        /* device time of the graph steps of the last hgks_batch_step call */
+    int last_steps;        /* steps of that call */
+} hgks_batch_info_t;
+/* handles: n distinct handles on one stream (n >= 1).  *out receives the
+ * batch.  Errors: INVALID_ARG (NULL, n < 1, a repeated handle, handles on
+ * different streams), CUDA (allocation of the work-lists). */
+hgks_status hgks_batch_create(hgks_t *handles, int n, hgks_batch_t *out);
+/* nsteps (>= 0) steps of every problem, each with its own CFL time step
+ * cfl * min over cells of dx_d / (|u_d| + c).  Work queued earlier on the
+ * handles' stream completes first; the call returns after the steps have
+ * completed.  The graph is captured on the first call and again whenever
+ * cfl or the tile size changes.  Errors: INVALID_ARG, NONFINITE (see above),
+ * CUDA. */
+hgks_status hgks_batch_step(hgks_batch_t b, int nsteps, double cfl);
+/* Autotuner: for each candidate sweep tile size (256, 1024, 4096, 16384
+ * positions) one warm-up and one timed graph step on the current states;
+ * keeps the fastest and restores every state and control block, so the
+ * problems are where they were.  Allocates a copy of the states for the
+ * duration of the call.  best_ms (may be NULL) receives the best step time.
+ * Errors: INVALID_ARG, CUDA. */
+hgks_status hgks_batch_tune(hgks_batch_t b, double cfl, double *best_ms);
+/* Fills *out.  Errors: INVALID_ARG (NULL). */
+hgks_status hgks_batch_info(hgks_batch_t b, hgks_batch_info_t *out);
+/* Message of the last error of this batch; owned by the batch. */
+const char *hgks_batch_last_error(hgks_batch_t b);
+/* Waits for the batch's work and frees it; the handles are untouched. */
+void hgks_batch_destroy(hgks_batch_t b);
+
 /* Device bytes a handle for this grid and precision allocates (admission). */
 size_t hgks_footprint_bytes(const hgks_grid *grid, hgks_precision precision);
 

@@ -9,6 +9,7 @@
 // All of it is enqueued on the handle's stream; the host reads the control
 // block once per hgks_step call to report a bad state.
 #include "../../include/hgks.h"
+#include "hgks_handle.h"
 #include "hgks_kernels.cuh"
 
 #include <algorithm>
@@ -20,24 +21,6 @@
 
 using namespace hgks;
 
-struct hgks_s {
-    Params P;
-    hgks_grid grid;
-    hgks_bcs bcs;
-    hgks_precision prec;
-    cudaStream_t st;
-    double *q[2] = { nullptr, nullptr };
-    int cur = 0;
-    double *qs = nullptr, *r = nullptr;
-    double *fq = nullptr, *t1 = nullptr;
-    double *F[3] = { nullptr, nullptr, nullptr };
-    double *io[2] = { nullptr, nullptr };  // interior staging buffers [5][N]
-    double *ytab = nullptr;                // y metric tables
-    double *stat_scratch = nullptr, *stat_out = nullptr;
-    Ctl *ctl = nullptr;
-    double rho_ref = 1.0;
-    std::string err;
-};
 
 static thread_local std::string g_err;
 

@@ -1,0 +1,579 @@
+// hgks_batch.cu -- many independent HGKS problems advanced together.
+//
+// A batch groups solver handles with their own grids (uneven sizes), gas
+// parameters, precisions and state buffers.  Every pass of a step runs as one
+// persistent kernel over a tile work-list that spans all problems: a tile is
+// a contiguous range of positions (interfaces or cells) of one problem, and
+// each block walks the tiles with a fixed stride, so small problems no longer
+// leave most of the GPU idle.  The 30 to 49 launches of a step are captured
+// once into a CUDA graph and replayed for every step.  Each problem keeps its own
+// control block: its time step, its bad-state flag (a bad problem stops
+// alone) and the index of its current state buffer, which the kernels read on
+// the device, so the same graph serves every step.  The tile size is picked by
+// a small autotuner (hgks_batch_tune) that times whole graph steps.
+#include "../../include/hgks.h"
+#include "hgks_passes.cuh"
+#include "hgks_passes_mx.cuh"
+
+#include "hgks_handle.h"
+
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+namespace hgks {
+
+void set_global_error(const char *msg);  // hgks_api.cu
+
+struct Inst {
+    Params P;
+    double *q[2], *qs, *r, *fq, *t1, *F[3];
+    Ctl *ctl;
+    int mixed, walls;
+    double lxlz;
+};
+
+struct Tile {
+    int inst;
+    int pad;
+    long long start, count;
+};
+
+// work-lists: ghost fill per direction, cells, then the three sweep passes
+// per direction, once for the FP64 problems and once for the mixed ones (so
+// each sweep kernel is compiled for one precision and keeps its registers)
+enum { WL_GHOST = 0, WL_CELLS = 3, WL_SWEEP = 4, WL_N = 22 };
+static inline int wl_sweep(int mixed, int pass, int d) { return WL_SWEEP + 9 * mixed + 3 * pass + d; }
+
+// ---------------------------------------------------------------------------
+// batched kernels: block b walks tiles b, b + gridDim.x, ...
+// ---------------------------------------------------------------------------
+__global__ void kb_ghost(const Inst *__restrict__ I, const Tile *__restrict__ T, int ntiles, int d, int stage)
+{
+    for (int k = blockIdx.x; k < ntiles; k += gridDim.x) {
+        const Tile tl = T[k];
+        const Inst &in = I[tl.inst];
+        double *q = stage == 0 ? in.q[in.ctl->good] : in.qs;
+        for (long long t = tl.start + threadIdx.x; t < tl.start + tl.count; t += blockDim.x) pos_ghost(in.P, q, d, t);
+    }
+}
+
+__global__ void kb_dt_reset(const Inst *__restrict__ I, int n)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) I[i].ctl->dtmin_bits = 0x7FF0000000000000ull;
+}
+
+__global__ void __launch_bounds__(256) kb_cfl(const Inst *__restrict__ I, const Tile *__restrict__ T, int ntiles)
+{
+    __shared__ double red[8];
+    for (int k = blockIdx.x; k < ntiles; k += gridDim.x) {
+        const Tile tl = T[k];
+        const Inst &in = I[tl.inst];
+        const double *q = in.q[in.ctl->good];
+        double v = INFINITY;
+        if (!in.ctl->flag)
+            for (long long t = tl.start + threadIdx.x; t < tl.start + tl.count; t += blockDim.x)
+                v = fmin(v, pos_cfl(in.P, q, t));
+        for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_down_sync(0xffffffffu, v, o));
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : INFINITY;
+            for (int o = 4; o > 0; o >>= 1) v = fmin(v, __shfl_down_sync(0xffffffffu, v, o));
+            if (threadIdx.x == 0 && v < INFINITY)
+                atomicMin(&in.ctl->dtmin_bits, (unsigned long long)__double_as_longlong(v));
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void kb_dt_final(const Inst *__restrict__ I, int n, double cfl)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || I[i].ctl->flag) return;
+    I[i].ctl->dt = cfl * __longlong_as_double((long long)I[i].ctl->dtmin_bits);
+}
+
+template <bool MX>
+__global__ void __launch_bounds__(128) kb_normal(const Inst *__restrict__ I, const Tile *__restrict__ T, int ntiles,
+                                                 int d, int stage)
+{
+    for (int k = blockIdx.x; k < ntiles; k += gridDim.x) {
+        const Tile tl = T[k];
+        const Inst &in = I[tl.inst];
+        if (in.ctl->flag) continue;
+        const double *q = stage == 0 ? in.q[in.ctl->good] : in.qs;
+        const Box B = box_fq(in.P, d);
+        if constexpr (MX) {
+            const long long nq = box_count(B);
+            for (long long t = tl.start + threadIdx.x; t < tl.start + tl.count; t += blockDim.x)
+                pos_normal_mx(in.P, d, B, q, in.fq, (float *)(in.fq + 15 * nq), t);
+        } else {
+            for (long long t = tl.start + threadIdx.x; t < tl.start + tl.count; t += blockDim.x)
+                pos_normal(in.P, d, B, q, in.fq, t);
+        }
+    }
+}
+
+template <bool MX>
+__global__ void __launch_bounds__(128) kb_tan1(const Inst *__restrict__ I, const Tile *__restrict__ T, int ntiles,
+                                               int d)
+{
+    for (int k = blockIdx.x; k < ntiles; k += gridDim.x) {
+        const Tile tl = T[k];
+        const Inst &in = I[tl.inst];
+        if (in.ctl->flag) continue;
+        const Box Bt = box_t1(in.P, d), Bq = box_fq(in.P, d);
+        if constexpr (MX) {
+            const long long nq = box_count(Bq), nt = box_count(Bt);
+            for (long long t = tl.start + threadIdx.x; t < tl.start + tl.count; t += blockDim.x)
+                pos_tan1_mx(in.P, d, Bt, Bq, in.fq, (const float *)(in.fq + 15 * nq), in.t1,
+                            (float *)(in.t1 + 50 * nt), t);
+        } else {
+            for (long long t = tl.start + threadIdx.x; t < tl.start + tl.count; t += blockDim.x)
+                pos_tan1(in.P, d, Bt, Bq, in.fq, in.t1, t);
+        }
+    }
+}
+
+template <bool MX>
+__global__ void __launch_bounds__(128) kb_flux(const Inst *__restrict__ I, const Tile *__restrict__ T, int ntiles,
+                                               int d)
+{
+    for (int k = blockIdx.x; k < ntiles; k += gridDim.x) {
+        const Tile tl = T[k];
+        const Inst &in = I[tl.inst];
+        if (in.ctl->flag) continue;
+        const Box Bf = box_face(in.P, d), Bt = box_t1(in.P, d);
+        const double dt = in.ctl->dt;
+        if constexpr (MX) {
+            const long long nt = box_count(Bt);
+            for (long long t = tl.start + threadIdx.x; t < tl.start + tl.count; t += blockDim.x)
+                pos_flux_mx(in.P, d, Bf, Bt, in.t1, (const float *)(in.t1 + 50 * nt), in.F[d], dt, t);
+        } else {
+            for (long long t = tl.start + threadIdx.x; t < tl.start + tl.count; t += blockDim.x)
+                pos_flux(in.P, d, Bf, Bt, in.t1, in.F[d], dt, t);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) kb_update(const Inst *__restrict__ I, const Tile *__restrict__ T, int ntiles,
+                                                 int stage)
+{
+    for (int k = blockIdx.x; k < ntiles; k += gridDim.x) {
+        const Tile tl = T[k];
+        const Inst &in = I[tl.inst];
+        if (in.ctl->flag) continue;
+        const int cur = in.ctl->good;
+        const double dt = in.ctl->dt;
+        bool ok = true;
+        for (long long t = tl.start + threadIdx.x; t < tl.start + tl.count; t += blockDim.x) {
+            if (stage == 1) ok &= pos_update(in.P, 1, in.q[cur], in.F[0], in.F[1], in.F[2], in.qs, in.r, dt, t);
+            else ok &= pos_update(in.P, 2, in.qs, in.F[0], in.F[1], in.F[2], in.q[1 - cur], in.r, dt, t);
+        }
+        if (!ok) atomicOr(&in.ctl->flag, 1);
+    }
+}
+
+// mean wall stress of each problem with y walls (one block per problem)
+__global__ void kb_wall(const Inst *__restrict__ I, int n)
+{
+    __shared__ double red[2][256];
+    const Inst &in = I[blockIdx.x];
+    if (!in.walls) return;
+    const int nx = in.P.n[0], ny = in.P.n[1], nz = in.P.n[2];
+    const long long n1 = (long long)nx * (ny + 1) * nz;
+    const double *Fy = in.F[1];
+    double lo = 0.0, hi = 0.0;
+    for (long long t = threadIdx.x; t < (long long)nx * nz; t += blockDim.x) {
+        int i = (int)(t % nx), k = (int)(t / nx);
+        lo += Fy[1 * n1 + ((long long)k * (ny + 1) + 0) * nx + i];
+        hi += Fy[1 * n1 + ((long long)k * (ny + 1) + ny) * nx + i];
+    }
+    red[0][threadIdx.x] = lo;
+    red[1][threadIdx.x] = hi;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) {
+            red[0][threadIdx.x] += red[0][threadIdx.x + s];
+            red[1][threadIdx.x] += red[1][threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && !in.ctl->flag) {
+        double s = 0.0;
+        int walls = 0;
+        if (in.P.bc_lo[1] == 1) { s += -red[0][0]; walls++; }
+        if (in.P.bc_hi[1] == 1) { s += red[1][0]; walls++; }
+        in.ctl->wall_shear = walls ? s / (walls * in.lxlz) : 0.0;
+    }
+}
+
+__global__ void kb_commit(const Inst *__restrict__ I, int n)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    Ctl *c = I[i].ctl;
+    if (c->flag) return;
+    c->t += c->dt;
+    c->step += 1;
+    c->last_dt = c->dt;
+    c->good = 1 - c->good;
+}
+
+}  // namespace hgks
+
+using namespace hgks;
+
+struct hgks_batch_s {
+    std::vector<hgks_t> h;
+    cudaStream_t user = nullptr;  // the problems' stream
+    cudaStream_t st = nullptr;    // the batch's own stream (graphs cannot be captured on the legacy stream)
+    Inst *d_inst = nullptr;
+    std::vector<Inst> inst;
+    Tile *d_tiles = nullptr;
+    int off[WL_N], cnt[WL_N];
+    long long tile_sweep = 2048, tile_cells = 8192;
+    int blocks_cells = 0, sms = 0;
+    int bsweep[2][3] = {};  // resident blocks of the normal, tan1 and flux kernels, per precision
+    bool any_walls = false;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    double graph_cfl = -1.0;
+    cudaEvent_t ev[2] = { nullptr, nullptr };
+    double last_ms = 0.0;
+    int last_steps = 0;
+    std::string err;
+};
+
+static hgks_status berr(hgks_batch_t b, hgks_status s, const std::string &m)
+{
+    if (b) b->err = m;
+    return s;
+}
+
+static void free_graph(hgks_batch_t b)
+{
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    b->graph_cfl = -1.0;
+}
+
+// tile work-lists of every pass for the current tile sizes
+static hgks_status build_tiles(hgks_batch_t b)
+{
+    std::vector<Tile> all;
+    auto add = [&](int, int i, long long total, long long ts) {
+        for (long long s = 0; s < total; s += ts) all.push_back(Tile{ i, 0, s, std::min(ts, total - s) });
+    };
+    for (int w = 0; w < WL_N; w++) {
+        b->off[w] = (int)all.size();
+        for (int i = 0; i < (int)b->inst.size(); i++) {
+            const Params &P = b->inst[i].P;
+            if (w < 3) add(w, i, ghost_count(P, w), b->tile_cells);
+            else if (w == WL_CELLS) add(w, i, P.ncell, b->tile_cells);
+            else {
+                const int mixed = (w - WL_SWEEP) / 9, pass = (w - WL_SWEEP) / 3 % 3, d = (w - WL_SWEEP) % 3;
+                if (mixed != b->inst[i].mixed) continue;
+                const Box B = pass == 0 ? box_fq(P, d) : pass == 1 ? box_t1(P, d) : box_face(P, d);
+                add(w, i, box_count(B), b->tile_sweep);
+            }
+        }
+        b->cnt[w] = (int)all.size() - b->off[w];
+    }
+    if (b->d_tiles) cudaFree(b->d_tiles);
+    b->d_tiles = nullptr;
+    cudaError_t e = cudaMalloc(&b->d_tiles, all.size() * sizeof(Tile));
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_tiles, all.data(), all.size() * sizeof(Tile), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return berr(b, HGKS_ERR_CUDA, std::string("tile list: ") + cudaGetErrorString(e));
+    free_graph(b);
+    return HGKS_OK;
+}
+
+static unsigned pgrid(int ntiles, int blocks) { return (unsigned)std::max(1, std::min(ntiles, blocks)); }
+
+static void enqueue_batch_step(hgks_batch_t b, double cfl)
+{
+    const Inst *I = b->d_inst;
+    const int n = (int)b->inst.size();
+    cudaStream_t st = b->st;
+    const unsigned ib = (unsigned)((n + 127) / 128);
+    auto T = [&](int w) { return b->d_tiles + b->off[w]; };
+    for (int d = 0; d < 3; d++) kb_ghost<<<pgrid(b->cnt[WL_GHOST + d], b->blocks_cells), 256, 0, st>>>(
+        I, T(WL_GHOST + d), b->cnt[WL_GHOST + d], d, 0);
+    kb_dt_reset<<<ib, 128, 0, st>>>(I, n);
+    kb_cfl<<<pgrid(b->cnt[WL_CELLS], b->blocks_cells), 256, 0, st>>>(I, T(WL_CELLS), b->cnt[WL_CELLS]);
+    kb_dt_final<<<ib, 128, 0, st>>>(I, n, cfl);
+    for (int stage = 0; stage < 2; stage++) {
+        if (stage == 1)
+            for (int d = 0; d < 3; d++) kb_ghost<<<pgrid(b->cnt[WL_GHOST + d], b->blocks_cells), 256, 0, st>>>(
+                I, T(WL_GHOST + d), b->cnt[WL_GHOST + d], d, 1);
+        for (int d = 0; d < 3; d++) {
+            for (int mx = 0; mx < 2; mx++) {
+                const int wn = wl_sweep(mx, 0, d), wt = wl_sweep(mx, 1, d), wf = wl_sweep(mx, 2, d);
+                if (!b->cnt[wn]) continue;  // no problem of this precision
+                if (mx) {
+                    kb_normal<true><<<pgrid(b->cnt[wn], b->bsweep[1][0]), 128, 0, st>>>(I, T(wn), b->cnt[wn], d,
+                                                                                       stage);
+                    kb_tan1<true><<<pgrid(b->cnt[wt], b->bsweep[1][1]), 128, 0, st>>>(I, T(wt), b->cnt[wt], d);
+                    kb_flux<true><<<pgrid(b->cnt[wf], b->bsweep[1][2]), 128, 0, st>>>(I, T(wf), b->cnt[wf], d);
+                } else {
+                    kb_normal<false><<<pgrid(b->cnt[wn], b->bsweep[0][0]), 128, 0, st>>>(I, T(wn), b->cnt[wn], d,
+                                                                                        stage);
+                    kb_tan1<false><<<pgrid(b->cnt[wt], b->bsweep[0][1]), 128, 0, st>>>(I, T(wt), b->cnt[wt], d);
+                    kb_flux<false><<<pgrid(b->cnt[wf], b->bsweep[0][2]), 128, 0, st>>>(I, T(wf), b->cnt[wf], d);
+                }
+            }
+            if (d == 1 && stage == 0 && b->any_walls) kb_wall<<<n, 256, 0, st>>>(I, n);
+        }
+        kb_update<<<pgrid(b->cnt[WL_CELLS], b->blocks_cells), 256, 0, st>>>(I, T(WL_CELLS), b->cnt[WL_CELLS],
+                                                                              stage + 1);
+    }
+    kb_commit<<<ib, 128, 0, st>>>(I, n);
+}
+
+static hgks_status capture(hgks_batch_t b, double cfl)
+{
+    free_graph(b);
+    cudaError_t e = cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return berr(b, HGKS_ERR_CUDA, std::string("begin capture: ") + cudaGetErrorString(e));
+    enqueue_batch_step(b, cfl);
+    e = cudaStreamEndCapture(b->st, &b->graph);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (e != cudaSuccess) {
+        free_graph(b);
+        return berr(b, HGKS_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    }
+    b->graph_cfl = cfl;
+    return HGKS_OK;
+}
+
+extern "C" hgks_status hgks_batch_create(hgks_t *handles, int n, hgks_batch_t *out)
+{
+    if (!handles || !out || n < 1) {
+        set_global_error("hgks_batch_create: need handles, out and n >= 1");
+        return HGKS_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    hgks_batch_t b = new hgks_batch_s();
+    b->user = handles[0] ? handles[0]->st : nullptr;
+    for (int i = 0; i < n; i++) {
+        hgks_t h = handles[i];
+        if (!h || h->st != b->user) {
+            delete b;
+            set_global_error("hgks_batch_create: a NULL handle, or handles on different streams");
+            return HGKS_ERR_INVALID_ARG;
+        }
+        for (int j = 0; j < i; j++)
+            if (handles[j] == h) {
+                delete b;
+                set_global_error("hgks_batch_create: a handle appears twice");
+                return HGKS_ERR_INVALID_ARG;
+            }
+        b->h.push_back(h);
+        Inst in;
+        memset(&in, 0, sizeof in);
+        in.P = h->P;
+        in.q[0] = h->q[0];
+        in.q[1] = h->q[1];
+        in.qs = h->qs;
+        in.r = h->r;
+        in.fq = h->fq;
+        in.t1 = h->t1;
+        for (int d = 0; d < 3; d++) in.F[d] = h->F[d];
+        in.ctl = h->ctl;
+        in.mixed = h->prec == HGKS_MIXED;
+        in.walls = h->P.bc_lo[1] == HGKS_BC_ISOTHERMAL_WALL || h->P.bc_hi[1] == HGKS_BC_ISOTHERMAL_WALL;
+        in.lxlz = h->grid.lx * h->grid.lz;
+        b->any_walls |= in.walls != 0;
+        b->inst.push_back(in);
+    }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+    // persistent grids: as many blocks as stay resident
+    int nb[2][3] = {};
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[0][0], kb_normal<false>, 128, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[0][1], kb_tan1<false>, 128, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[0][2], kb_flux<false>, 128, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[1][0], kb_normal<true>, 128, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[1][1], kb_tan1<true>, 128, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[1][2], kb_flux<true>, 128, 0);
+    for (int m = 0; m < 2; m++)
+        for (int p = 0; p < 3; p++) b->bsweep[m][p] = std::max(1, nb[m][p]) * b->sms;
+    b->blocks_cells = b->sms * 8;
+    cudaError_t e = cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&b->ev[0]);
+    if (e == cudaSuccess) e = cudaEventCreate(&b->ev[1]);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_inst, n * sizeof(Inst));
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_inst, b->inst.data(), n * sizeof(Inst), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        set_global_error((std::string("hgks_batch_create: ") + cudaGetErrorString(e)).c_str());
+        hgks_batch_destroy(b);
+        return HGKS_ERR_CUDA;
+    }
+    hgks_status s = build_tiles(b);
+    if (s) {
+        hgks_batch_destroy(b);
+        return s;
+    }
+    *out = b;
+    return HGKS_OK;
+}
+
+extern "C" void hgks_batch_destroy(hgks_batch_t b)
+{
+    if (!b) return;
+    if (b->st) cudaStreamSynchronize(b->st);
+    free_graph(b);
+    if (b->d_tiles) cudaFree(b->d_tiles);
+    if (b->d_inst) cudaFree(b->d_inst);
+    for (int i = 0; i < 2; i++)
+        if (b->ev[i]) cudaEventDestroy(b->ev[i]);
+    if (b->st) cudaStreamDestroy(b->st);
+    delete b;
+}
+
+extern "C" const char *hgks_batch_last_error(hgks_batch_t b) { return b ? b->err.c_str() : "null batch"; }
+
+// read every problem's control block: sync the host's buffer index, clear flags
+static hgks_status batch_finish(hgks_batch_t b)
+{
+    cudaError_t e = cudaStreamSynchronize(b->st);
+    if (e != cudaSuccess) return berr(b, HGKS_ERR_CUDA, std::string("batch step: ") + cudaGetErrorString(e));
+    int bad = -1;
+    for (size_t i = 0; i < b->h.size(); i++) {
+        Ctl c;
+        e = cudaMemcpy(&c, b->h[i]->ctl, sizeof c, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return berr(b, HGKS_ERR_CUDA, cudaGetErrorString(e));
+        b->h[i]->cur = c.good;
+        if (c.flag) {
+            if (bad < 0) bad = (int)i;
+            c.flag = 0;
+            e = cudaMemcpy(b->h[i]->ctl, &c, sizeof c, cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) return berr(b, HGKS_ERR_CUDA, cudaGetErrorString(e));
+        }
+    }
+    if (bad >= 0)
+        return berr(b, HGKS_ERR_NONFINITE, "problem " + std::to_string(bad) +
+                                               " produced a bad state; it (and any other) stayed at its last "
+                                               "completed step, the others advanced");
+    return HGKS_OK;
+}
+
+extern "C" hgks_status hgks_batch_step(hgks_batch_t b, int nsteps, double cfl)
+{
+    if (!b || nsteps < 0 || !(cfl > 0.0)) return berr(b, HGKS_ERR_INVALID_ARG, "need nsteps >= 0 and cfl > 0");
+    // work already queued on the problems' stream comes first
+    cudaError_t e0 = cudaStreamSynchronize(b->user);
+    if (e0 != cudaSuccess) return berr(b, HGKS_ERR_CUDA, cudaGetErrorString(e0));
+    if (!b->exec || b->graph_cfl != cfl) {
+        hgks_status s = capture(b, cfl);
+        if (s) return s;
+    }
+    cudaEventRecord(b->ev[0], b->st);
+    for (int k = 0; k < nsteps; k++) {
+        cudaError_t e = cudaGraphLaunch(b->exec, b->st);
+        if (e != cudaSuccess) return berr(b, HGKS_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+    }
+    cudaEventRecord(b->ev[1], b->st);
+    hgks_status s = batch_finish(b);
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]) == cudaSuccess) {
+        b->last_ms = ms;
+        b->last_steps = nsteps;
+    }
+    return s;
+}
+
+extern "C" hgks_status hgks_batch_info(hgks_batch_t b, hgks_batch_info_t *out)
+{
+    if (!b || !out) return HGKS_ERR_INVALID_ARG;
+    out->problems = (int)b->h.size();
+    out->tile_sweep = (int)b->tile_sweep;
+    out->tile_cells = (int)b->tile_cells;
+    // ghost 6, dt 3, update 2, commit 1, wall 0/1, and 3 sweep passes x 3
+    // directions x 2 stages for each precision present
+    int prec = 0;
+    for (int mx = 0; mx < 2; mx++) prec += b->cnt[wl_sweep(mx, 0, 0)] ? 1 : 0;
+    out->launches_per_step = 12 + 18 * prec + (b->any_walls ? 1 : 0);
+    long long tiles = 0;
+    for (int w = 0; w < WL_N; w++) tiles += b->cnt[w];
+    out->tiles = tiles;
+    out->last_ms = b->last_ms;
+    out->last_steps = b->last_steps;
+    return HGKS_OK;
+}
+
+// time whole graph steps for each candidate tile size on copies of the
+// states, keep the fastest, restore the states
+extern "C" hgks_status hgks_batch_tune(hgks_batch_t b, double cfl, double *best_ms)
+{
+    if (!b || !(cfl > 0.0)) return berr(b, HGKS_ERR_INVALID_ARG, "need cfl > 0");
+    const int n = (int)b->h.size();
+    // snapshot states and control blocks
+    std::vector<double *> saved(n, nullptr);
+    std::vector<Ctl> ctl(n);
+    cudaError_t e = cudaStreamSynchronize(b->user);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
+    for (int i = 0; i < n && e == cudaSuccess; i++) {
+        size_t bytes = (size_t)b->inst[i].P.cs * 5 * sizeof(double);
+        e = cudaMalloc(&saved[i], 2 * bytes);
+        if (e == cudaSuccess) e = cudaMemcpy(saved[i], b->h[i]->q[0], bytes, cudaMemcpyDeviceToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(saved[i] + bytes / sizeof(double), b->h[i]->q[1], bytes, cudaMemcpyDeviceToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(&ctl[i], b->h[i]->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost);
+    }
+    auto restore = [&]() {
+        cudaError_t r = cudaStreamSynchronize(b->st);
+        for (int i = 0; i < n && r == cudaSuccess; i++) {
+            size_t bytes = (size_t)b->inst[i].P.cs * 5 * sizeof(double);
+            r = cudaMemcpy(b->h[i]->q[0], saved[i], bytes, cudaMemcpyDeviceToDevice);
+            if (r == cudaSuccess) r = cudaMemcpy(b->h[i]->q[1], saved[i] + bytes / sizeof(double), bytes, cudaMemcpyDeviceToDevice);
+            if (r == cudaSuccess) r = cudaMemcpy(b->h[i]->ctl, &ctl[i], sizeof(Ctl), cudaMemcpyHostToDevice);
+            b->h[i]->cur = ctl[i].good;
+        }
+        return r;
+    };
+    const long long cand[] = { 256, 1024, 4096, 16384 };
+    double best = 1e300;
+    long long best_ts = b->tile_sweep;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    for (long long ts : cand) {
+        if (e != cudaSuccess) break;
+        b->tile_sweep = ts;
+        if (build_tiles(b) != HGKS_OK || capture(b, cfl) != HGKS_OK) {
+            e = cudaErrorUnknown;
+            break;
+        }
+        cudaGraphLaunch(b->exec, b->st);  // warm-up
+        cudaEventRecord(e0, b->st);
+        cudaGraphLaunch(b->exec, b->st);
+        cudaEventRecord(e1, b->st);
+        e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && ms < best) {
+            best = ms;
+            best_ts = ts;
+        }
+        if (e == cudaSuccess) e = restore();
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaError_t r = restore();
+    for (int i = 0; i < n; i++)
+        if (saved[i]) cudaFree(saved[i]);
+    if (e != cudaSuccess || r != cudaSuccess)
+        return berr(b, HGKS_ERR_CUDA, std::string("tuning: ") + cudaGetErrorString(e != cudaSuccess ? e : r));
+    b->tile_sweep = best_ts;
+    hgks_status s = build_tiles(b);
+    if (s) return s;
+    if (best_ms) *best_ms = best;
+    return HGKS_OK;
+}

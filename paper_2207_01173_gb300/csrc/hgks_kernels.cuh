@@ -21,10 +21,36 @@ constexpr int FQ_N = 30;   // Ql, Qr, dQl, dQr, Q0, dQ0 (x5 components), normal 
 constexpr int T1_N = 110;  // per Gauss line (2): 25 WENO values, 15 linear values, 15 linear derivatives
 constexpr int F_N = 10;    // F^n and dF^n/dt (x5 components), global component order
 
-// boxes of sweep d
-Box box_fq(const Params &P, int d);
-Box box_t1(const Params &P, int d);
-Box box_face(const Params &P, int d);
+// boxes of sweep d: the normal pass (all faces, two tangential ghost rows
+// each side), the first tangential pass (ghost rows along t2 only), the faces
+__host__ __device__ inline Box box_fq(const Params &P, int d)
+{
+    Box b;
+    for (int e = 0; e < 3; e++) {
+        b.E[e] = e == d ? P.n[e] + 1 : P.n[e] + 4;
+        b.O[e] = e == d ? 0 : -2;
+    }
+    return b;
+}
+__host__ __device__ inline Box box_t1(const Params &P, int d)
+{
+    Box b;
+    const int t2 = tdir(d, 1);
+    for (int e = 0; e < 3; e++) {
+        b.E[e] = e == d ? P.n[e] + 1 : (e == t2 ? P.n[e] + 4 : P.n[e]);
+        b.O[e] = e == t2 ? -2 : 0;
+    }
+    return b;
+}
+__host__ __device__ inline Box box_face(const Params &P, int d)
+{
+    Box b;
+    for (int e = 0; e < 3; e++) {
+        b.E[e] = e == d ? P.n[e] + 1 : P.n[e];
+        b.O[e] = 0;
+    }
+    return b;
+}
 
 // launches (all on `st`)
 void launch_ghost(const Params &P, double *q, cudaStream_t st);

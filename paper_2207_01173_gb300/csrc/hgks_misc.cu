@@ -1,6 +1,6 @@
 // hgks_misc.cu -- ghost fill, time step, stage update, diagnostics and initial
 // fields of the HGKS step (FP64), arXiv 2207.01173 Sec. 2 and Sec. 4.
-#include "hgks_kernels.cuh"
+#include "hgks_passes.cuh"
 
 namespace hgks {
 
@@ -11,78 +11,16 @@ static inline unsigned grid_for(long long n, int bs) { return (unsigned)((n + bs
 // Directions are filled in the order x, y, z, each over the already filled
 // extent of the earlier directions, so edges and corners are filled too.
 // ---------------------------------------------------------------------------
-static __device__ void wall_ghost(const Params &P, const double s[5], double o[5])
-{
-    // mirror: U_g = -U_i, p_g = p_i, T_g = 2 T_w - T_i (floored at T_w / 2), rho_g = p_g / T_g
-    double ir = 1.0 / s[0];
-    double U = s[1] * ir, V = s[2] * ir, W = s[3] * ir;
-    double p = (P.gamma - 1.0) * (s[4] - 0.5 * s[0] * (U * U + V * V + W * W));
-    double T = p / s[0];
-    double Tg = 2.0 * P.T_wall - T;
-    if (Tg < 0.5 * P.T_wall) Tg = 0.5 * P.T_wall;
-    double rho = p / Tg;
-    o[0] = rho;
-    o[1] = -rho * U;
-    o[2] = -rho * V;
-    o[3] = -rho * W;
-    o[4] = p / (P.gamma - 1.0) + 0.5 * rho * (U * U + V * V + W * W);
-}
-
 __global__ void k_ghost(Params P, double *q, int d)
 {
-    // the two other directions in increasing order; earlier directions span the padded range
-    const int ea = d == 0 ? 1 : 0, eb = d == 2 ? 1 : 2;
-    const int loa = ea < d ? -NG : 0, Ra = ea < d ? P.n[ea] + 2 * NG : P.n[ea];
-    const int lob = eb < d ? -NG : 0, Rb = eb < d ? P.n[eb] + 2 * NG : P.n[eb];
-    const long long total = (long long)2 * NG * Ra * Rb;
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= total) return;
-    int g, ca, cb;
-    if (d == 0) {  // ghost index fastest (x is the ghost direction)
-        g = (int)(t % (2 * NG));
-        long long r = t / (2 * NG);
-        ca = (int)(r % Ra) + loa;
-        cb = (int)(r / Ra) + lob;
-    } else {       // x fastest
-        ca = (int)(t % Ra) + loa;
-        long long r = t / Ra;
-        g = (int)(r % (2 * NG));
-        cb = (int)(r / (2 * NG)) + lob;
-    }
-    const int side = g / NG, m = g % NG, n = P.n[d];
-    const int gi = side == 0 ? -1 - m : n + m;
-    const int bc = side == 0 ? P.bc_lo[d] : P.bc_hi[d];
-    int si;
-    if (bc == 0) si = ((gi % n) + n) % n;
-    else si = side == 0 ? m : n - 1 - m;
-    int ig[3], is[3];
-    ig[d] = gi;
-    is[d] = si;
-    ig[ea] = is[ea] = ca;
-    ig[eb] = is[eb] = cb;
-    const long long pg = pidx(P, ig[0], ig[1], ig[2]), ps = pidx(P, is[0], is[1], is[2]);
-    if (bc == 0) {
-#pragma unroll
-        for (int c = 0; c < 5; c++) q[c * P.cs + pg] = q[c * P.cs + ps];
-    } else {
-        double s[5], o[5];
-#pragma unroll
-        for (int c = 0; c < 5; c++) s[c] = q[c * P.cs + ps];
-        wall_ghost(P, s, o);
-#pragma unroll
-        for (int c = 0; c < 5; c++) q[c * P.cs + pg] = o[c];
-    }
+    if (t >= ghost_count(P, d)) return;
+    pos_ghost(P, q, d, t);
 }
 
 void launch_ghost(const Params &P, double *q, cudaStream_t st)
 {
-    for (int d = 0; d < 3; d++) {
-        const int ea = d == 0 ? 1 : 0, eb = d == 2 ? 1 : 2;
-        long long Ra = ea < d ? P.n[ea] + 2 * NG : P.n[ea];
-        long long Rb = eb < d ? P.n[eb] + 2 * NG : P.n[eb];
-        long long total = 2LL * NG * Ra * Rb;
-        k_ghost<<<grid_for(total, 256), 256, 0, st>>>(P, q, d);
-    }
+    for (int d = 0; d < 3; d++) k_ghost<<<grid_for(ghost_count(P, d), 256), 256, 0, st>>>(P, q, d);
 }
 
 // ---------------------------------------------------------------------------
@@ -95,17 +33,7 @@ __global__ void __launch_bounds__(256) k_cfl(Params P, const double *__restrict_
     __shared__ double red[8];
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     double v = INFINITY;
-    if (t < P.ncell && !ctl->flag) {
-        int i = (int)(t % P.n[0]);
-        long long r = t / P.n[0];
-        int j = (int)(r % P.n[1]), k = (int)(r / P.n[1]);
-        long long p = pidx(P, i, j, k);
-        double rho = q[p], ir = 1.0 / rho;
-        double U = q[P.cs + p] * ir, V = q[2 * P.cs + p] * ir, W = q[3 * P.cs + p] * ir;
-        double pr = (P.gamma - 1.0) * (q[4 * P.cs + p] - 0.5 * rho * (U * U + V * V + W * W));
-        double c = sqrt(P.gamma * pr * ir);
-        v = fmin(P.h[0] / (fabs(U) + c), fmin(P.hy_cell[j] / (fabs(V) + c), P.h[2] / (fabs(W) + c)));
-    }
+    if (t < P.ncell && !ctl->flag) v = pos_cfl(P, q, t);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_down_sync(0xffffffffu, v, o));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
@@ -140,49 +68,6 @@ void launch_set_dt(Ctl *ctl, double dt, cudaStream_t st) { k_set_dt<<<1, 1, 0, s
 // ---------------------------------------------------------------------------
 // flux divergence (Eq. "semi2"), body force and the S2O4 stages (Eq. "two-stage")
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void cell_rhs(const Params &P, const double *q, const double *const F[3], int i, int j,
-                                         int k, long long p, double L[5], double dL[5])
-{
-    const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
-    const long long n0 = (long long)(nx + 1) * ny * nz, n1 = (long long)nx * (ny + 1) * nz,
-                    n2 = (long long)nx * ny * (nz + 1);
-    const long long l0 = ((long long)k * ny + j) * (nx + 1) + i;
-    const long long l1 = ((long long)k * (ny + 1) + j) * nx + i;
-    const long long l2 = ((long long)k * ny + j) * nx + i;
-    const double vol = P.h[0] * P.hy_cell[j] * P.h[2];
-#pragma unroll
-    for (int c = 0; c < 5; c++) {
-        double sx = F[0][c * n0 + l0 + 1] - F[0][c * n0 + l0];
-        double sy = F[1][c * n1 + l1 + nx] - F[1][c * n1 + l1];
-        double sz = F[2][c * n2 + l2 + (long long)nx * ny] - F[2][c * n2 + l2];
-        L[c] = -((sx + sy) + sz) / vol;
-        double tx = F[0][(5 + c) * n0 + l0 + 1] - F[0][(5 + c) * n0 + l0];
-        double ty = F[1][(5 + c) * n1 + l1 + nx] - F[1][(5 + c) * n1 + l1];
-        double tz = F[2][(5 + c) * n2 + l2 + (long long)nx * ny] - F[2][(5 + c) * n2 + l2];
-        dL[c] = -((tx + ty) + tz) / vol;
-    }
-    if (P.has_force) {
-        // source (0, rho G, rho u.G) and its time derivative (0, G L_rho, G.L_mom)
-        const double rho = q[p], m0 = q[P.cs + p], m1 = q[2 * P.cs + p], m2 = q[3 * P.cs + p];
-        L[1] += rho * P.G[0];
-        L[2] += rho * P.G[1];
-        L[3] += rho * P.G[2];
-        L[4] += m0 * P.G[0] + m1 * P.G[1] + m2 * P.G[2];
-        dL[1] += P.G[0] * L[0];
-        dL[2] += P.G[1] * L[0];
-        dL[3] += P.G[2] * L[0];
-        dL[4] += P.G[0] * L[1] + P.G[1] * L[2] + P.G[2] * L[3];
-    }
-}
-
-__device__ __forceinline__ bool state_ok(const double Q[5])
-{
-    bool fin = isfinite(Q[0]) && isfinite(Q[1]) && isfinite(Q[2]) && isfinite(Q[3]) && isfinite(Q[4]);
-    if (!fin || !(Q[0] > 0.0)) return false;
-    double e = Q[4] - 0.5 * (Q[1] * Q[1] + Q[2] * Q[2] + Q[3] * Q[3]) / Q[0];
-    return e > 0.0;
-}
-
 __global__ void __launch_bounds__(256) k_update(Params P, int stage, const double *__restrict__ q,
                                                 const double *__restrict__ F0, const double *__restrict__ F1,
                                                 const double *__restrict__ F2, double *__restrict__ oa,
@@ -190,36 +75,7 @@ __global__ void __launch_bounds__(256) k_update(Params P, int stage, const doubl
 {
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= P.ncell || ctl->flag) return;
-    const double dt = ctl->dt;
-    int i = (int)(t % P.n[0]);
-    long long r = t / P.n[0];
-    int j = (int)(r % P.n[1]), k = (int)(r / P.n[1]);
-    const long long p = pidx(P, i, j, k);
-    const double *F[3] = { F0, F1, F2 };
-    double L[5], dL[5], A[5];
-    cell_rhs(P, q, F, i, j, k, p, L, dL);
-    bool ok = true;
-    if (stage == 1) {
-        double B[5];
-#pragma unroll
-        for (int c = 0; c < 5; c++) {
-            double Q = q[c * P.cs + p];
-            A[c] = Q + 0.5 * dt * L[c] + 0.125 * dt * dt * dL[c];
-            B[c] = Q + dt * L[c] + (dt * dt / 6.0) * dL[c];
-            oa[c * P.cs + p] = A[c];
-            ob[c * P.cs + p] = B[c];
-        }
-        ok = state_ok(A);
-    } else {
-        // oa = r + dt^2/3 dL(Q*), r = the stage-1 accumulator passed as ob
-#pragma unroll
-        for (int c = 0; c < 5; c++) {
-            A[c] = ob[c * P.cs + p] + (dt * dt / 3.0) * dL[c];
-            oa[c * P.cs + p] = A[c];
-        }
-        ok = state_ok(A);
-    }
-    if (!ok) atomicOr(&ctl->flag, 1);
+    if (!pos_update(P, stage, q, F0, F1, F2, oa, ob, ctl->dt, t)) atomicOr(&ctl->flag, 1);
 }
 
 void launch_update(const Params &P, int stage, const double *q, const double *const F[3], double *out_a,

@@ -74,6 +74,15 @@ class FlopModel(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class BatchInfo(C.Structure):
+    _fields_ = [("problems", C.c_int), ("tile_sweep", C.c_int), ("tile_cells", C.c_int),
+                ("launches_per_step", C.c_int), ("tiles", C.c_longlong), ("last_ms", C.c_double),
+                ("last_steps", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _D = C.POINTER(C.c_double)
 _lib = None
 
@@ -81,7 +90,9 @@ _lib = None
 EXPORTS = ("hgks_create", "hgks_init_tgv", "hgks_init_channel", "hgks_init_density_wave", "hgks_set_state",
            "hgks_get_state", "hgks_set_time", "hgks_step", "hgks_step_dt", "hgks_compute_dt", "hgks_rhs",
            "hgks_stats", "hgks_footprint_bytes", "hgks_last_error", "hgks_synchronize", "hgks_destroy",
-           "hgks_step_timed", "hgks_fp64_probe", "hgks_flop_model", "hgks_cfl_dt_noalloc")
+           "hgks_step_timed", "hgks_fp64_probe", "hgks_flop_model", "hgks_cfl_dt_noalloc",
+           "hgks_batch_create", "hgks_batch_step", "hgks_batch_tune", "hgks_batch_info", "hgks_batch_last_error",
+           "hgks_batch_destroy")
 
 
 def library_path():
@@ -122,8 +133,17 @@ def lib(build_if_missing=True):
         L.hgks_flop_model.argtypes = [C.POINTER(Grid), C.c_int, C.POINTER(FlopModel)]
         L.hgks_cfl_dt_noalloc.argtypes = [C.POINTER(Grid), C.c_double, C.c_double, C.c_void_p, C.c_void_p,
                                           C.c_void_p]
+        L.hgks_batch_create.argtypes = [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_void_p)]
+        L.hgks_batch_step.argtypes = [C.c_void_p, C.c_int, C.c_double]
+        L.hgks_batch_tune.argtypes = [C.c_void_p, C.c_double, _D]
+        L.hgks_batch_info.argtypes = [C.c_void_p, C.POINTER(BatchInfo)]
+        L.hgks_batch_last_error.argtypes = [C.c_void_p]
+        L.hgks_batch_last_error.restype = C.c_char_p
+        L.hgks_batch_destroy.argtypes = [C.c_void_p]
+        L.hgks_batch_destroy.restype = None
         for name in EXPORTS:
-            if name not in ("hgks_footprint_bytes", "hgks_last_error", "hgks_destroy"):
+            if name not in ("hgks_footprint_bytes", "hgks_last_error", "hgks_destroy", "hgks_batch_last_error",
+                            "hgks_batch_destroy"):
                 getattr(L, name).restype = S
         _lib = L
     return _lib
@@ -304,3 +324,49 @@ class Solver:
         if a.dtype != torch.float64:
             raise ValueError("expected float64")
         return C.c_void_p(a.data_ptr()), a
+
+
+class Batch:
+    """Several Solver problems advanced together: one persistent kernel per
+    pass over a tile work-list spanning all of them, one CUDA graph per step.
+
+    Keep the solvers alive while the batch exists; close the batch first."""
+
+    def __init__(self, solvers):
+        self.b = None
+        self.solvers = list(solvers)
+        arr = (C.c_void_p * len(self.solvers))(*[sv.h.value for sv in self.solvers])
+        b = C.c_void_p()
+        st = lib().hgks_batch_create(arr, len(self.solvers), C.byref(b))
+        if st != HGKS_OK:
+            raise HgksError(st, lib().hgks_last_error(None).decode())
+        self.b = b
+
+    def _check(self, st):
+        if st != HGKS_OK:
+            raise HgksError(st, lib().hgks_batch_last_error(self.b).decode())
+
+    def step(self, nsteps=1, cfl=0.5):
+        self._check(lib().hgks_batch_step(self.b, nsteps, cfl))
+
+    def tune(self, cfl=0.5):
+        """Pick the sweep tile size by timing graph steps; returns the best step time in ms."""
+        ms = C.c_double()
+        self._check(lib().hgks_batch_tune(self.b, cfl, C.byref(ms)))
+        return ms.value
+
+    def info(self):
+        i = BatchInfo()
+        self._check(lib().hgks_batch_info(self.b, C.byref(i)))
+        return i.as_dict()
+
+    def close(self):
+        if self.b:
+            lib().hgks_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -59,3 +59,13 @@ def test_invalid_arguments_rejected_before_device():
     with pytest.raises(hgks.HgksError) as e:
         hgks.Solver((8, 2, 8), bc_lo=(0, 1, 0), bc_hi=(0, 1, 0))
     assert e.value.status == hgks.HGKS_ERR_INVALID_ARG
+
+
+def test_batch_workload_is_seeded_and_in_range():
+    from paper_2207_01173_gb300.workloads import batch_tgv_problems
+    a, b = batch_tgv_problems(), batch_tgv_problems()
+    assert a == b and len(a) == 64
+    for n, Ma, Re in a:
+        assert all(v in (24, 32, 48, 64, 96) for v in n)
+        assert 0.1 <= Ma <= 0.5 and 400.0 <= Re <= 3200.0
+    assert len({n for n, _, _ in a}) > 20  # uneven grids
