@@ -220,6 +220,7 @@ def run_ours(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     import paper_2207_01173_gb300 as hg
+    from paper_2207_01173_gb300.decomp import max_over_ranks
 
     n = args.n
     cells = n ** 3
@@ -247,11 +248,7 @@ def run_ours(args, rank, world, local_rank):
             if world > 1:
                 dist.barrier()
             torch.cuda.synchronize()
-        ms = ev0.elapsed_time(ev1)
-        if world > 1:
-            t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ev0.elapsed_time(ev1), device="cuda")
         return ms, times, clk.summary()
 
     ms, times, clocks = timed_run(solver)
@@ -303,11 +300,7 @@ def run_ours(args, rank, world, local_rank):
         solver.step(1, CFL)
         solver.get_state(out_host)
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, device="cuda")
     e2e_value = world * cells * e2e_steps / e2e_s
     stats = solver.stats()
 

@@ -534,6 +534,9 @@ struct hgks_ref_s {
     double *yface;       /* ny+1 face coordinates of the (possibly stretched) y mesh */
     double t, dt_last, wall_shear;
     int64_t step;
+    hgks_ref_halo_fn halo_hook;
+    hgks_ref_min_fn min_hook;
+    void *hook_user;
     char err[256];
 };
 
@@ -621,6 +624,7 @@ static void ghost_fill(const hgks_ref_t h, double *q)
                     for (int m = 0; m < NG; m++) {
                         int g = side == 0 ? -1 - m : n + m;
                         int bc = side == 0 ? h->bcs.lo[d] : h->bcs.hi[d];
+                        if (bc == HGKS_REF_BC_EXTERNAL) continue;
                         int s;
                         if (bc == HGKS_REF_BC_PERIODIC) s = ((g % n) + n) % n;
                         else s = side == 0 ? m : n - 1 - m;
@@ -640,6 +644,7 @@ static void ghost_fill(const hgks_ref_t h, double *q)
                         }
                     }
     }
+    if (h->halo_hook) h->halo_hook(h->hook_user, q);
 }
 
 /* ---- time step (Alg. 1 STEP 1; R-DT: convective, per direction) ---- */
@@ -1148,7 +1153,18 @@ int hgks_ref_set_time(hgks_ref_t h, double t, int64_t step)
 int hgks_ref_compute_dt(hgks_ref_t h, double cfl, double *dt)
 {
     if (!h || !dt || !(cfl > 0.0)) return HGKS_REF_ERR_INVALID_ARG;
-    *dt = cfl * dt_limit(h, h->q);
+    double m = dt_limit(h, h->q);
+    if (h->min_hook) m = h->min_hook(h->hook_user, m);
+    *dt = cfl * m;
+    return HGKS_REF_OK;
+}
+
+int hgks_ref_set_hooks(hgks_ref_t h, hgks_ref_halo_fn halo, hgks_ref_min_fn dtmin, void *user)
+{
+    if (!h) return HGKS_REF_ERR_INVALID_ARG;
+    h->halo_hook = halo;
+    h->min_hook = dtmin;
+    h->hook_user = user;
     return HGKS_REF_OK;
 }
 
@@ -1259,7 +1275,9 @@ int hgks_ref_step(hgks_ref_t h, int nsteps, double cfl)
     if (st) return fail(h, st, "out of memory");
     for (int s = 0; s < nsteps; s++) {
         ghost_fill(h, h->q);
-        double dt = cfl * dt_limit(h, h->q);
+        double m = dt_limit(h, h->q);
+        if (h->min_hook) m = h->min_hook(h->hook_user, m);
+        double dt = cfl * m;
         st = one_step(h, dt);
         if (st) return st;
     }

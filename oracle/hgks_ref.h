@@ -28,7 +28,9 @@ typedef struct hgks_ref_s *hgks_ref_t;
 
 enum { HGKS_REF_OK = 0, HGKS_REF_ERR_INVALID_ARG = 1, HGKS_REF_ERR_OOM = 2,
        HGKS_REF_ERR_NONFINITE = 4, HGKS_REF_ERR_STATE = 6 };
-enum { HGKS_REF_BC_PERIODIC = 0, HGKS_REF_BC_ISOTHERMAL_WALL = 1 };
+/* EXTERNAL: the ghost layers of that side are left to the caller (filled by
+   the halo hook below); used to emulate a slab decomposition with CPU ranks */
+enum { HGKS_REF_BC_PERIODIC = 0, HGKS_REF_BC_ISOTHERMAL_WALL = 1, HGKS_REF_BC_EXTERNAL = 2 };
 enum { HGKS_REF_VISC_CONSTANT = 0, HGKS_REF_VISC_POWER = 1 };
 
 typedef struct { int nx, ny, nz; double lx, ly, lz; double x0, y0, z0;
@@ -55,6 +57,13 @@ int  hgks_ref_rhs(hgks_ref_t h, double dt, double *L, double *dL); /* L(Q), dL/d
 /* L, dL/dt at sampled interior cells (index (k ny + j) nx + i); outputs [ncells][5] */
 int  hgks_ref_rhs_cells(hgks_ref_t h, double dt, int ncells, const int64_t *cells, double *L, double *dL);
 int  hgks_ref_stats(hgks_ref_t h, hgks_ref_stats_t *out);
+/* Hooks for slab ranks.  halo(user, q) runs after every ghost fill of a
+   padded state q ([5][nz+6][ny+6][nx+6]; the physical boundary ghosts are
+   already set, EXTERNAL ones are the hook's to write).  dtmin(user, m)
+   turns this rank's CFL minimum m into the global one.  NULL: no hook. */
+typedef void (*hgks_ref_halo_fn)(void *user, double *q);
+typedef double (*hgks_ref_min_fn)(void *user, double local_min);
+int  hgks_ref_set_hooks(hgks_ref_t h, hgks_ref_halo_fn halo, hgks_ref_min_fn dtmin, void *user);
 const char *hgks_ref_last_error(hgks_ref_t h);
 void hgks_ref_destroy(hgks_ref_t h);
 

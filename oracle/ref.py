@@ -10,7 +10,10 @@ import numpy as np
 
 from .build import build_oracle
 
-BC_PERIODIC, BC_WALL = 0, 1
+BC_PERIODIC, BC_WALL, BC_EXTERNAL = 0, 1, 2
+HALO_FN = C.CFUNCTYPE(None, C.c_void_p, C.POINTER(C.c_double))
+MIN_FN = C.CFUNCTYPE(C.c_double, C.c_void_p, C.c_double)
+NG = 3
 VISC_CONSTANT, VISC_POWER = 0, 1
 
 
@@ -98,6 +101,7 @@ def lib():
         L.hgks_ref_quartic_coeffs.restype = None
         L.hgks_ref_splitmix64.argtypes = [C.c_uint64]
         L.hgks_ref_splitmix64.restype = C.c_uint64
+        L.hgks_ref_set_hooks.argtypes = [C.c_void_p, HALO_FN, MIN_FN, C.c_void_p]
         _lib = L
     return _lib
 
@@ -171,6 +175,22 @@ class RefSolver:
 
     def set_time(self, t, step):
         self._check(lib().hgks_ref_set_time(self.h, t, step), "set_time")
+
+    def set_hooks(self, halo=None, dtmin=None):
+        """halo(q) receives every ghost-filled padded state as a writable
+        array [5][nz+6][ny+6][nx+6]; dtmin(m) maps this rank's CFL minimum to
+        the global one.  None removes a hook."""
+        nx, ny, nz = self.n
+        shape = (5, nz + 2 * NG, ny + 2 * NG, nx + 2 * NG)
+
+        def _halo(user, ptr):
+            halo(np.ctypeslib.as_array(ptr, shape=shape))
+
+        def _min(user, m):
+            return float(dtmin(m))
+
+        self._hooks = (HALO_FN(_halo) if halo else HALO_FN(), MIN_FN(_min) if dtmin else MIN_FN())
+        self._check(lib().hgks_ref_set_hooks(self.h, self._hooks[0], self._hooks[1], None), "set_hooks")
 
     def step(self, nsteps=1, cfl=0.5):
         self._check(lib().hgks_ref_step(self.h, nsteps, cfl), "step")
