@@ -206,6 +206,37 @@ def batched_leg(hg, args, stream):
     return out
 
 
+def serve_leg(hg, args, capacity):
+    """The serving workload: a seeded Poisson stream of Taylor-Green and
+    channel solves in mixed precision, served by the continuous-batching loop
+    with admission by device footprint.  The arrival rate is 0.8 of the
+    measured capacity (cell-updates/s of the batched mixed path) divided by
+    the mean work per request of the whole 500-request stream; the first
+    --serve-requests requests of that stream are served."""
+    import torch
+    from paper_2207_01173_gb300 import workloads
+    from paper_2207_01173_gb300.serve import CudaEngine, Server
+
+    stream = workloads.serve_requests()
+    mean_work = float(np.mean([workloads.request_work(r) for r in stream]))
+    rate = 0.8 * capacity / mean_work
+    reqs = [dict(r, t=r["arrival"] / rate) for r in stream[:args.serve_requests]]
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(min(0.8 * free, args.serve_budget_gb * 2 ** 30))
+    eng = CudaEngine(precision=hg.MIXED, cfl=CFL)
+    srv = Server(eng, budget, max_chunk=args.serve_chunk)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        res, summ = srv.run(reqs)
+    eng.close()
+    summ.update(workload="Poisson stream (seed 500) of Taylor-Green (60%%, N in {32..192}) and channel (40%%, "
+                         "N in {64,96,128}) solves of 20-200 steps, mixed precision; first %d of 500 requests"
+                % len(reqs),
+                arrival_rate_per_s=rate, capacity_cell_updates_per_s=capacity, mean_work_cell_updates=mean_work,
+                max_chunk=args.serve_chunk, batch_rebuilds=eng.rebuilds, clocks=clk.summary(),
+                latency_percentiles="numpy linear interpolation over completed requests")
+    return summ
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -306,6 +337,10 @@ def run_ours(args, rank, world, local_rank):
 
     solver.close()
     batched = None if args.no_batched else batched_leg(hg, args, stream)
+    serve = None
+    if rank == 0 and args.serve_requests > 0:
+        cap = batched["mixed"]["value"] if batched else (mixed["value"] if mixed else value)
+        serve = serve_leg(hg, args, cap)
 
     if rank != 0:
         return 0
@@ -341,6 +376,7 @@ def run_ours(args, rank, world, local_rank):
         "cpu_baseline": cpu_baseline,
         "mixed": mixed,
         "batched": batched,
+        "serve": serve,
         "final_stats": {"t": stats["t"], "step": stats["step"], "Ek": stats["Ek"], "enstrophy": stats["enstrophy"]},
     }
     print(json.dumps(line), flush=True)
@@ -361,6 +397,9 @@ def main():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=3)
+    ap.add_argument("--serve-requests", type=int, default=12)
+    ap.add_argument("--serve-budget-gb", type=float, default=96.0)
+    ap.add_argument("--serve-chunk", type=int, default=8)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")

@@ -271,6 +271,11 @@ hgks_status hgks_batch_step(hgks_batch_t b, int nsteps, double cfl);
  * duration of the call.  best_ms (may be NULL) receives the best step time.
  * Errors: INVALID_ARG, CUDA. */
 hgks_status hgks_batch_tune(hgks_batch_t b, double cfl, double *best_ms);
+/* steps[i] receives the step counter of problem i as read back at the end
+ * of the last hgks_batch_step call (no device work); a problem that stopped
+ * on a bad state shows fewer steps than the others.  steps: n entries, owned
+ * by the caller.  Errors: INVALID_ARG (NULL), STATE (no step call yet). */
+hgks_status hgks_batch_steps(hgks_batch_t b, long long *steps);
 /* Fills *out.  Errors: INVALID_ARG (NULL). */
 hgks_status hgks_batch_info(hgks_batch_t b, hgks_batch_info_t *out);
 /* Message of the last error of this batch; owned by the batch. */

@@ -245,6 +245,7 @@ struct hgks_batch_s {
     cudaEvent_t ev[2] = { nullptr, nullptr };
     double last_ms = 0.0;
     int last_steps = 0;
+    std::vector<long long> steps;  // step counters read at the end of the last call
     std::string err;
 };
 
@@ -446,11 +447,13 @@ static hgks_status batch_finish(hgks_batch_t b)
     cudaError_t e = cudaStreamSynchronize(b->st);
     if (e != cudaSuccess) return berr(b, HGKS_ERR_CUDA, std::string("batch step: ") + cudaGetErrorString(e));
     int bad = -1;
+    b->steps.assign(b->h.size(), 0);
     for (size_t i = 0; i < b->h.size(); i++) {
         Ctl c;
         e = cudaMemcpy(&c, b->h[i]->ctl, sizeof c, cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return berr(b, HGKS_ERR_CUDA, cudaGetErrorString(e));
         b->h[i]->cur = c.good;
+        b->steps[i] = (long long)c.step;
         if (c.flag) {
             if (bad < 0) bad = (int)i;
             c.flag = 0;
@@ -488,6 +491,14 @@ extern "C" hgks_status hgks_batch_step(hgks_batch_t b, int nsteps, double cfl)
         b->last_steps = nsteps;
     }
     return s;
+}
+
+extern "C" hgks_status hgks_batch_steps(hgks_batch_t b, long long *steps)
+{
+    if (!b || !steps) return berr(b, HGKS_ERR_INVALID_ARG, "need steps");
+    if (b->steps.size() != b->h.size()) return berr(b, HGKS_ERR_STATE, "no hgks_batch_step call yet");
+    for (size_t i = 0; i < b->h.size(); i++) steps[i] = b->steps[i];
+    return HGKS_OK;
 }
 
 extern "C" hgks_status hgks_batch_info(hgks_batch_t b, hgks_batch_info_t *out)

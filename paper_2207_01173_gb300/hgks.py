@@ -91,8 +91,8 @@ EXPORTS = ("hgks_create", "hgks_init_tgv", "hgks_init_channel", "hgks_init_densi
            "hgks_get_state", "hgks_set_time", "hgks_step", "hgks_step_dt", "hgks_compute_dt", "hgks_rhs",
            "hgks_stats", "hgks_footprint_bytes", "hgks_last_error", "hgks_synchronize", "hgks_destroy",
            "hgks_step_timed", "hgks_fp64_probe", "hgks_flop_model", "hgks_cfl_dt_noalloc",
-           "hgks_batch_create", "hgks_batch_step", "hgks_batch_tune", "hgks_batch_info", "hgks_batch_last_error",
-           "hgks_batch_destroy")
+           "hgks_batch_create", "hgks_batch_step", "hgks_batch_tune", "hgks_batch_steps", "hgks_batch_info",
+           "hgks_batch_last_error", "hgks_batch_destroy")
 
 
 def library_path():
@@ -137,6 +137,7 @@ def lib(build_if_missing=True):
         L.hgks_batch_step.argtypes = [C.c_void_p, C.c_int, C.c_double]
         L.hgks_batch_tune.argtypes = [C.c_void_p, C.c_double, _D]
         L.hgks_batch_info.argtypes = [C.c_void_p, C.POINTER(BatchInfo)]
+        L.hgks_batch_steps.argtypes = [C.c_void_p, C.POINTER(C.c_longlong)]
         L.hgks_batch_last_error.argtypes = [C.c_void_p]
         L.hgks_batch_last_error.restype = C.c_char_p
         L.hgks_batch_destroy.argtypes = [C.c_void_p]
@@ -354,6 +355,12 @@ class Batch:
         ms = C.c_double()
         self._check(lib().hgks_batch_tune(self.b, cfl, C.byref(ms)))
         return ms.value
+
+    def steps(self):
+        """Step counter of each problem after the last step call."""
+        a = (C.c_longlong * len(self.solvers))()
+        self._check(lib().hgks_batch_steps(self.b, a))
+        return list(a)
 
     def info(self):
         i = BatchInfo()
