@@ -15,7 +15,7 @@ VISC_POWER = 1
 
 
 def tgv_solver_kwargs(Ma, Re, gamma=GAMMA):
-    """Solver keyword arguments of a Taylor-Green vortex (Section 5.1): unit
+    """Solver keyword arguments of a Taylor-Green vortex (Sec. 4.1): unit
     velocity and density scale, mean pressure 1/(gamma Ma^2), power-law
     viscosity mu = (1/Re) (T/T0)^0.7 with T0 the mean temperature p0/rho0."""
     p0 = 1.0 / (gamma * Ma * Ma)
@@ -37,7 +37,7 @@ def batch_tgv_problems(count=64, seed=64, sizes=(24, 32, 48, 64, 96)):
 
 
 def channel_solver_kwargs(Ma=0.5, Reb=2800.0, Re_tau=180.0, gamma=GAMMA):
-    """Solver keyword arguments of the compressible channel (Section 5.2):
+    """Solver keyword arguments of the compressible channel (Sec. 4.2):
     box 2pi x 2 x pi, y in [-1, 1] stretched with b = 2, isothermal walls at
     the bulk temperature 1/(gamma Ma^2), power-law viscosity 1/Re_b at that
     temperature, Pr 0.7, and a constant streamwise body force
