@@ -30,6 +30,11 @@ sys.path.insert(0, ROOT)
 GAMMA = 1.4
 MA, RE, PR, OMEGA, CFL = 0.1, 1600.0, 0.72, 0.7, 0.5
 METRIC = "cell-updates/s TGV 256^3 FP64 vs mixed at stated error; serve p50/p99 ms"
+# DRAM bytes per face of one k_flux launch (dram__bytes_read.sum +
+# dram__bytes_write.sum from an ncu capture of this k_flux on TGV 64^3,
+# 722.7 MB for 266,240 faces); scaled by the faces of a launch.  Must be
+# re-measured whenever k_flux changes.
+K_FLUX_DRAM_BYTES_PER_FACE = 722688256 / 266240
 # Table 3 of the paper: 256^3 TGV, FP64, Tesla V100, 11.697 h for 20 t_c at dt = 8.925e-4
 PAPER_V100_CUPS = 256 ** 3 * (20.0 / 8.925e-4) / (11.697 * 3600.0)
 
@@ -360,7 +365,8 @@ def run_ours(args, rank, world, local_rank):
         "vs_baseline": value / PAPER_V100_CUPS, "dtype": "f64", "data": "synthetic",
         "config": dict(workload_config(n), parallelism=("replicas%d" % world) if world > 1 else "single-gpu"),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": "k_flux",
+                     "frac": achieved / peak, "traffic": K_FLUX_DRAM_BYTES_PER_FACE * faces_per_launch,
+                     "traffic_note": "ncu DRAM bytes of one TGV 64^3 launch scaled by faces", "kernel": "k_flux",
                      "peak_note": "nominal GB300 dense FP64 (1.25 TFLOP/s); measured FP64 FMA probe %.3f TFLOP/s"
                                   % fp64_peak,
                      "algorithmic_flops_per_launch": flops_per_launch,
