@@ -89,11 +89,11 @@ static Sizes sizes_of(const Params &P)
 
 extern "C" size_t hgks_footprint_bytes(const hgks_grid *grid, hgks_precision precision)
 {
-    (void)precision;
     if (!grid || grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return 0;
     Params P = shape_params(*grid);
     Sizes s = sizes_of(P);
     size_t doubles = 4 * s.pad + s.fq + s.t1 + s.F[0] + s.F[1] + s.F[2] + 2 * s.cells + s.ytab + s.stats;
+    if (precision == HGKS_MIXED) doubles += s.pad;  // the split state
     return doubles * sizeof(double) + sizeof(Ctl);
 }
 
@@ -142,7 +142,7 @@ static std::vector<double> y_tables(const hgks_grid &g)
 // ---------------------------------------------------------------------------
 static void free_all(hgks_t h)
 {
-    double *bufs[] = { h->q[0], h->q[1], h->qs, h->r, h->fq, h->t1, h->F[0], h->F[1], h->F[2],
+    double *bufs[] = { h->q[0], h->q[1], h->qs, h->r, h->fq, h->t1, h->qf, h->F[0], h->F[1], h->F[2],
                        h->io[0], h->io[1], h->ytab, h->stat_scratch, h->stat_out };
     for (double *b : bufs)
         if (b) cudaFree(b);
@@ -209,6 +209,14 @@ extern "C" hgks_status hgks_create(const hgks_grid *grid, double gamma, double P
     P.T_wall = bcs->T_wall;
     for (int d = 0; d < 3; d++) P.G[d] = body_force ? body_force[d] : 0.0;
     P.has_force = (P.G[0] != 0.0 || P.G[1] != 0.0 || P.G[2] != 0.0);
+    P.f_gm1 = (float)(gamma - 1.0);
+    P.f_gm1_lo = (float)((gamma - 1.0) - (double)P.f_gm1);
+    P.f_K = (float)P.K;
+    P.f_prc = (float)(1.0 / Pr - 1.0);
+    P.f_mu_ref = (float)P.mu_ref;
+    P.f_inv_Tref = (float)(1.0 / P.T_ref);
+    P.f_omega = (float)P.omega;
+    for (int d = 0; d < 3; d++) P.f_ih[d] = (float)(1.0 / P.h[d]);
 
     Sizes s = sizes_of(P);
     auto alloc = [&](double **p, size_t n) -> hgks_status {
@@ -221,6 +229,7 @@ extern "C" hgks_status hgks_create(const hgks_grid *grid, double gamma, double P
     if (!st) st = alloc(&h->r, s.pad);
     if (!st) st = alloc(&h->fq, s.fq);
     if (!st) st = alloc(&h->t1, s.t1);
+    if (!st && precision == HGKS_MIXED) st = alloc(&h->qf, s.pad);
     for (int d = 0; d < 3 && !st; d++) st = alloc(&h->F[d], s.F[d]);
     if (!st) st = alloc(&h->io[0], s.cells);
     if (!st) st = alloc(&h->io[1], s.cells);
@@ -393,14 +402,18 @@ static void enqueue_sweeps(hgks_t h, const double *q, bool record_wall, StepTime
 {
     const Params &P = h->P;
     const bool mixed = h->prec == HGKS_MIXED;
+    if (mixed) {
+        launch_split_mixed(P, q, h->qf, h->ctl, h->st);
+        mark(T, TK_OTHER);
+    }
     for (int d = 0; d < 3; d++) {
-        if (mixed) launch_sweep_mixed(P, d, q, h->fq, h->t1, h->F[d], h->ctl, h->st, 0);
+        if (mixed) launch_sweep_mixed(P, d, h->qf, h->fq, h->t1, h->F[d], h->ctl, h->st, 0);
         else launch_normal(P, d, q, h->fq, h->ctl, h->st);
         mark(T, TK_NORMAL);
-        if (mixed) launch_sweep_mixed(P, d, q, h->fq, h->t1, h->F[d], h->ctl, h->st, 1);
+        if (mixed) launch_sweep_mixed(P, d, h->qf, h->fq, h->t1, h->F[d], h->ctl, h->st, 1);
         else launch_tan1(P, d, h->fq, h->t1, h->ctl, h->st);
         mark(T, TK_TAN1);
-        if (mixed) launch_sweep_mixed(P, d, q, h->fq, h->t1, h->F[d], h->ctl, h->st, 2);
+        if (mixed) launch_sweep_mixed(P, d, h->qf, h->fq, h->t1, h->F[d], h->ctl, h->st, 2);
         else launch_flux(P, d, h->t1, h->F[d], h->ctl, h->st);
         mark(T, TK_FLUX);
         if (d == 1 && record_wall && (P.bc_lo[1] == HGKS_BC_ISOTHERMAL_WALL || P.bc_hi[1] == HGKS_BC_ISOTHERMAL_WALL)) {

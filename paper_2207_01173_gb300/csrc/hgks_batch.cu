@@ -5,7 +5,7 @@
 // persistent kernel over a tile work-list that spans all problems: a tile is
 // a contiguous range of positions (interfaces or cells) of one problem, and
 // each block walks the tiles with a fixed stride, so small problems no longer
-// leave most of the GPU idle.  The 30 to 49 launches of a step are captured
+// leave most of the GPU idle.  The 30 to 51 launches of a step are captured
 // once into a CUDA graph and replayed for every step.  Each problem keeps its own
 // control block: its time step, its bad-state flag (a bad problem stops
 // alone) and the index of its current state buffer, which the kernels read on
@@ -29,6 +29,7 @@ void set_global_error(const char *msg);  // hgks_api.cu
 struct Inst {
     Params P;
     double *q[2], *qs, *r, *fq, *t1, *F[3];
+    float *qh, *ql;  // mixed: the split state
     Ctl *ctl;
     int mixed, walls;
     double lxlz;
@@ -43,7 +44,7 @@ struct Tile {
 // work-lists: ghost fill per direction, cells, then the three sweep passes
 // per direction, once for the FP64 problems and once for the mixed ones (so
 // each sweep kernel is compiled for one precision and keeps its registers)
-enum { WL_GHOST = 0, WL_CELLS = 3, WL_SWEEP = 4, WL_N = 22 };
+enum { WL_GHOST = 0, WL_CELLS = 3, WL_SWEEP = 4, WL_PAD = 22, WL_N = 23 };  // WL_PAD: padded cells, mixed only
 static inline int wl_sweep(int mixed, int pass, int d) { return WL_SWEEP + 9 * mixed + 3 * pass + d; }
 
 // ---------------------------------------------------------------------------
@@ -56,6 +57,20 @@ __global__ void kb_ghost(const Inst *__restrict__ I, const Tile *__restrict__ T,
         const Inst &in = I[tl.inst];
         double *q = stage == 0 ? in.q[in.ctl->good] : in.qs;
         for (long long t = tl.start + threadIdx.x; t < tl.start + tl.count; t += blockDim.x) pos_ghost(in.P, q, d, t);
+    }
+}
+
+// mixed problems: split the state of this stage into hi / lo float planes
+__global__ void __launch_bounds__(256) kb_split(const Inst *__restrict__ I, const Tile *__restrict__ T, int ntiles,
+                                                int stage)
+{
+    for (int k = blockIdx.x; k < ntiles; k += gridDim.x) {
+        const Tile tl = T[k];
+        const Inst &in = I[tl.inst];
+        if (in.ctl->flag) continue;
+        const double *q = stage == 0 ? in.q[in.ctl->good] : in.qs;
+        for (long long t = tl.start + threadIdx.x; t < tl.start + tl.count; t += blockDim.x)
+            pos_split_mx(in.P, q, in.qh, in.ql, t);
     }
 }
 
@@ -107,9 +122,9 @@ __global__ void __launch_bounds__(128) kb_normal(const Inst *__restrict__ I, con
         const double *q = stage == 0 ? in.q[in.ctl->good] : in.qs;
         const Box B = box_fq(in.P, d);
         if constexpr (MX) {
-            const long long nq = box_count(B);
+            const FqMx o = fq_mx(in.fq, box_count(B));
             for (long long t = tl.start + threadIdx.x; t < tl.start + tl.count; t += blockDim.x)
-                pos_normal_mx(in.P, d, B, q, in.fq, (float *)(in.fq + 15 * nq), t);
+                pos_normal_mx(in.P, d, B, in.qh, in.ql, o, t);
         } else {
             for (long long t = tl.start + threadIdx.x; t < tl.start + tl.count; t += blockDim.x)
                 pos_normal(in.P, d, B, q, in.fq, t);
@@ -118,7 +133,7 @@ __global__ void __launch_bounds__(128) kb_normal(const Inst *__restrict__ I, con
 }
 
 template <bool MX>
-__global__ void __launch_bounds__(128) kb_tan1(const Inst *__restrict__ I, const Tile *__restrict__ T, int ntiles,
+__global__ void __launch_bounds__(128, MX ? 4 : 1) kb_tan1(const Inst *__restrict__ I, const Tile *__restrict__ T, int ntiles,
                                                int d)
 {
     for (int k = blockIdx.x; k < ntiles; k += gridDim.x) {
@@ -127,10 +142,10 @@ __global__ void __launch_bounds__(128) kb_tan1(const Inst *__restrict__ I, const
         if (in.ctl->flag) continue;
         const Box Bt = box_t1(in.P, d), Bq = box_fq(in.P, d);
         if constexpr (MX) {
-            const long long nq = box_count(Bq), nt = box_count(Bt);
+            const FqMx fi = fq_mx(in.fq, box_count(Bq));
+            const T1Mx o = t1_mx(in.t1, box_count(Bt));
             for (long long t = tl.start + threadIdx.x; t < tl.start + tl.count; t += blockDim.x)
-                pos_tan1_mx(in.P, d, Bt, Bq, in.fq, (const float *)(in.fq + 15 * nq), in.t1,
-                            (float *)(in.t1 + 50 * nt), t);
+                pos_tan1_mx(in.P, d, Bt, Bq, fi, o, t);
         } else {
             for (long long t = tl.start + threadIdx.x; t < tl.start + tl.count; t += blockDim.x)
                 pos_tan1(in.P, d, Bt, Bq, in.fq, in.t1, t);
@@ -138,7 +153,25 @@ __global__ void __launch_bounds__(128) kb_tan1(const Inst *__restrict__ I, const
     }
 }
 
-template <bool MX>
+// The mixed flux pass is the one pass that is not persistent: it launches one
+// block per tile of exactly FLUX_MX_TILE positions (one per thread), and the
+// hardware block scheduler hands out the tiles.  A persistent loop keeps its
+// state live across the flux, which at the 128-register budget of this
+// latency-bound kernel raised the spills from 48 to 232 bytes and cost 40 %.
+constexpr int FLUX_MX_TILE = 128;
+
+__global__ void __launch_bounds__(FLUX_MX_TILE, 4) kb_flux_mx(const Inst *__restrict__ I,
+                                                              const Tile *__restrict__ T, int ntiles, int d)
+{
+    const int k = blockIdx.x;
+    if (k >= ntiles) return;
+    const Tile tl = T[k];
+    const Inst &in = I[tl.inst];
+    if (in.ctl->flag || (long long)threadIdx.x >= tl.count) return;
+    const Box Bf = box_face(in.P, d), Bt = box_t1(in.P, d);
+    pos_flux_mx(in.P, d, Bf, Bt, t1_mx(in.t1, box_count(Bt)), in.F[d], in.ctl->dt, tl.start + threadIdx.x);
+}
+
 __global__ void __launch_bounds__(128) kb_flux(const Inst *__restrict__ I, const Tile *__restrict__ T, int ntiles,
                                                int d)
 {
@@ -148,14 +181,8 @@ __global__ void __launch_bounds__(128) kb_flux(const Inst *__restrict__ I, const
         if (in.ctl->flag) continue;
         const Box Bf = box_face(in.P, d), Bt = box_t1(in.P, d);
         const double dt = in.ctl->dt;
-        if constexpr (MX) {
-            const long long nt = box_count(Bt);
-            for (long long t = tl.start + threadIdx.x; t < tl.start + tl.count; t += blockDim.x)
-                pos_flux_mx(in.P, d, Bf, Bt, in.t1, (const float *)(in.t1 + 50 * nt), in.F[d], dt, t);
-        } else {
-            for (long long t = tl.start + threadIdx.x; t < tl.start + tl.count; t += blockDim.x)
-                pos_flux(in.P, d, Bf, Bt, in.t1, in.F[d], dt, t);
-        }
+        for (long long t = tl.start + threadIdx.x; t < tl.start + tl.count; t += blockDim.x)
+            pos_flux(in.P, d, Bf, Bt, in.t1, in.F[d], dt, t);
     }
 }
 
@@ -277,11 +304,13 @@ static hgks_status build_tiles(hgks_batch_t b)
             const Params &P = b->inst[i].P;
             if (w < 3) add(w, i, ghost_count(P, w), b->tile_cells);
             else if (w == WL_CELLS) add(w, i, P.ncell, b->tile_cells);
-            else {
+            else if (w == WL_PAD) {
+                if (b->inst[i].mixed) add(w, i, P.cs, b->tile_cells);
+            } else {
                 const int mixed = (w - WL_SWEEP) / 9, pass = (w - WL_SWEEP) / 3 % 3, d = (w - WL_SWEEP) % 3;
                 if (mixed != b->inst[i].mixed) continue;
                 const Box B = pass == 0 ? box_fq(P, d) : pass == 1 ? box_t1(P, d) : box_face(P, d);
-                add(w, i, box_count(B), b->tile_sweep);
+                add(w, i, box_count(B), (mixed && pass == 2) ? FLUX_MX_TILE : b->tile_sweep);
             }
         }
         b->cnt[w] = (int)all.size() - b->off[w];
@@ -313,6 +342,8 @@ static void enqueue_batch_step(hgks_batch_t b, double cfl)
         if (stage == 1)
             for (int d = 0; d < 3; d++) kb_ghost<<<pgrid(b->cnt[WL_GHOST + d], b->blocks_cells), 256, 0, st>>>(
                 I, T(WL_GHOST + d), b->cnt[WL_GHOST + d], d, 1);
+        if (b->cnt[WL_PAD])
+            kb_split<<<pgrid(b->cnt[WL_PAD], b->blocks_cells), 256, 0, st>>>(I, T(WL_PAD), b->cnt[WL_PAD], stage);
         for (int d = 0; d < 3; d++) {
             for (int mx = 0; mx < 2; mx++) {
                 const int wn = wl_sweep(mx, 0, d), wt = wl_sweep(mx, 1, d), wf = wl_sweep(mx, 2, d);
@@ -321,12 +352,12 @@ static void enqueue_batch_step(hgks_batch_t b, double cfl)
                     kb_normal<true><<<pgrid(b->cnt[wn], b->bsweep[1][0]), 128, 0, st>>>(I, T(wn), b->cnt[wn], d,
                                                                                        stage);
                     kb_tan1<true><<<pgrid(b->cnt[wt], b->bsweep[1][1]), 128, 0, st>>>(I, T(wt), b->cnt[wt], d);
-                    kb_flux<true><<<pgrid(b->cnt[wf], b->bsweep[1][2]), 128, 0, st>>>(I, T(wf), b->cnt[wf], d);
+                    kb_flux_mx<<<(unsigned)b->cnt[wf], FLUX_MX_TILE, 0, st>>>(I, T(wf), b->cnt[wf], d);
                 } else {
                     kb_normal<false><<<pgrid(b->cnt[wn], b->bsweep[0][0]), 128, 0, st>>>(I, T(wn), b->cnt[wn], d,
                                                                                         stage);
                     kb_tan1<false><<<pgrid(b->cnt[wt], b->bsweep[0][1]), 128, 0, st>>>(I, T(wt), b->cnt[wt], d);
-                    kb_flux<false><<<pgrid(b->cnt[wf], b->bsweep[0][2]), 128, 0, st>>>(I, T(wf), b->cnt[wf], d);
+                    kb_flux<<<pgrid(b->cnt[wf], b->bsweep[0][2]), 128, 0, st>>>(I, T(wf), b->cnt[wf], d);
                 }
             }
             if (d == 1 && stage == 0 && b->any_walls) kb_wall<<<n, 256, 0, st>>>(I, n);
@@ -388,6 +419,8 @@ extern "C" hgks_status hgks_batch_create(hgks_t *handles, int n, hgks_batch_t *o
         for (int d = 0; d < 3; d++) in.F[d] = h->F[d];
         in.ctl = h->ctl;
         in.mixed = h->prec == HGKS_MIXED;
+        in.qh = (float *)h->qf;
+        in.ql = in.qh ? in.qh + 5 * h->P.cs : nullptr;
         in.walls = h->P.bc_lo[1] == HGKS_BC_ISOTHERMAL_WALL || h->P.bc_hi[1] == HGKS_BC_ISOTHERMAL_WALL;
         in.lxlz = h->grid.lx * h->grid.lz;
         b->any_walls |= in.walls != 0;
@@ -400,10 +433,10 @@ extern "C" hgks_status hgks_batch_create(hgks_t *handles, int n, hgks_batch_t *o
     int nb[2][3] = {};
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[0][0], kb_normal<false>, 128, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[0][1], kb_tan1<false>, 128, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[0][2], kb_flux<false>, 128, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[0][2], kb_flux, 128, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[1][0], kb_normal<true>, 128, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[1][1], kb_tan1<true>, 128, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[1][2], kb_flux<true>, 128, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[1][2], kb_flux_mx, FLUX_MX_TILE, 0);
     for (int m = 0; m < 2; m++)
         for (int p = 0; p < 3; p++) b->bsweep[m][p] = std::max(1, nb[m][p]) * b->sms;
     b->blocks_cells = b->sms * 8;
@@ -507,11 +540,12 @@ extern "C" hgks_status hgks_batch_info(hgks_batch_t b, hgks_batch_info_t *out)
     out->problems = (int)b->h.size();
     out->tile_sweep = (int)b->tile_sweep;
     out->tile_cells = (int)b->tile_cells;
-    // ghost 6, dt 3, update 2, commit 1, wall 0/1, and 3 sweep passes x 3
-    // directions x 2 stages for each precision present
+    // ghost 6, dt 3, update 2, commit 1, wall 0/1, split 2 when a mixed
+    // problem is present, and 3 sweep passes x 3 directions x 2 stages for
+    // each precision present
     int prec = 0;
     for (int mx = 0; mx < 2; mx++) prec += b->cnt[wl_sweep(mx, 0, 0)] ? 1 : 0;
-    out->launches_per_step = 12 + 18 * prec + (b->any_walls ? 1 : 0);
+    out->launches_per_step = 12 + 18 * prec + (b->cnt[WL_PAD] ? 2 : 0) + (b->any_walls ? 1 : 0);
     long long tiles = 0;
     for (int w = 0; w < WL_N; w++) tiles += b->cnt[w];
     out->tiles = tiles;

@@ -50,6 +50,10 @@ struct Params {
     int has_force;
     int bc_lo[3], bc_hi[3];
     double T_wall;
+    // FP32 copies for the mixed-precision passes: gamma - 1 as a float-float
+    // pair, K, 1/Pr - 1, the viscosity law, and 1/h of the uniform directions
+    float f_gm1, f_gm1_lo, f_K, f_prc, f_mu_ref, f_inv_Tref, f_omega;
+    float f_ih[3];
 };
 
 // device control block of one handle
@@ -172,8 +176,8 @@ struct Prim {
     T rho, U, V, W, lam;
 };
 
-template <typename T>
-HGKS_HD Prim<T> prim_of(const T Q[5], double K)
+template <typename T, typename S>
+HGKS_HD Prim<T> prim_of(const T Q[5], S K)
 {
     Prim<T> g;
     T ir = T(1.0) / Q[0];
@@ -261,8 +265,8 @@ struct Gas {
     T rho, ir, U[3], uu, p, Tm, tl, lam, E;  // tl = 2 lambda = 1/T, E = rho E
 };
 
-template <typename T>
-HGKS_HD Gas<T> gas_of(const T Q[5], double gm1)
+template <typename T, typename S>
+HGKS_HD Gas<T> gas_of(const T Q[5], S gm1)
 {
     Gas<T> g;
     g.rho = Q[0];
@@ -280,8 +284,8 @@ HGKS_HD Gas<T> gas_of(const T Q[5], double gm1)
 }
 
 // directional derivative of the Euler flux F_D (D = 0 normal, 1, 2) along dQ
-template <int D, typename T>
-HGKS_HD void euler_dflux(const Gas<T> &g, const T dQ[5], double gm1, T o[5])
+template <int D, typename T, typename S>
+HGKS_HD void euler_dflux(const Gas<T> &g, const T dQ[5], S gm1, T o[5])
 {
     const T dp = T(gm1) * (dQ[4] - (g.U[0] * dQ[1] + g.U[1] * dQ[2] + g.U[2] * dQ[3]) + T(0.5) * g.uu * dQ[0]);
     const T dUd = (dQ[1 + D] - g.U[D] * dQ[0]) * g.ir;
@@ -298,8 +302,8 @@ HGKS_HD void euler_dflux(const Gas<T> &g, const T dQ[5], double gm1, T o[5])
 // H_D = (rho U Ud + p d0D,
 //        rho U Ud U_k + p (d0D U_k + d0k Ud + dDk U),
 //        U Ud (rho E + 2p) + d0D p (|U|^2 + (K+5) T) / 2)
-template <int D, typename T>
-HGKS_HD void second_dmoment(const Gas<T> &g, const T dQ[5], double gm1, double Kp5, T o[5])
+template <int D, typename T, typename S>
+HGKS_HD void second_dmoment(const Gas<T> &g, const T dQ[5], S gm1, S Kp5, T o[5])
 {
     const T drho = dQ[0];
     T dU[3];
@@ -359,8 +363,8 @@ struct HalfSide {
     T uU[5], uT[5], vV[4], vT[4], wW[4], wT[4];  // their partial derivatives
 };
 
-template <typename T>
-HGKS_HD void half_side_setup(const T Q[5], double gm1, double K, bool pos, HalfSide<T> &h)
+template <typename T, typename S>
+HGKS_HD void half_side_setup(const T Q[5], S gm1, S K, bool pos, HalfSide<T> &h)
 {
     h.rho = Q[0];
     h.ir = T(1.0) / Q[0];
@@ -431,8 +435,8 @@ struct HalfDelta {
     T rho, du[5], dv[4], dw[4], dxi1;
 };
 
-template <typename T>
-HGKS_HD void half_delta(const HalfSide<T> &h, const T dQ[5], double gm1, double K, HalfDelta<T> &d)
+template <typename T, typename S>
+HGKS_HD void half_delta(const HalfSide<T> &h, const T dQ[5], S gm1, S K, HalfDelta<T> &d)
 {
     const T dU = (dQ[1] - h.U[0] * dQ[0]) * h.ir;
     const T dV = (dQ[2] - h.U[1] * dQ[0]) * h.ir;
@@ -473,8 +477,8 @@ HGKS_HD void half_dphi(const HalfSide<T> &h, const HalfDelta<T> &d, T o[5])
 }
 
 // time change of the conserved variables of an Euler state: d_t Q = -sum_d DF_d(Q)[d_d Q]
-template <typename T>
-HGKS_HD void euler_dtq(const Gas<T> &g, const T dq[3][5], double gm1, T o[5])
+template <typename T, typename S>
+HGKS_HD void euler_dtq(const Gas<T> &g, const T dq[3][5], S gm1, T o[5])
 {
     T s[5];
     euler_dflux<0>(g, dq[0], gm1, o);
@@ -488,8 +492,8 @@ HGKS_HD void euler_dtq(const Gas<T> &g, const T dq[3][5], double gm1, T o[5])
 
 // all half-range terms of one side: Q0 part and B4 (values), W5, B5 (slopes),
 // W6, B6 (time slope), summed over the three derivative directions
-template <typename T>
-HGKS_HD void half_terms(const T Q[5], const T dq[3][5], double gm1, double K, bool pos, T q0[5], T b4[5],
+template <typename T, typename S>
+HGKS_HD void half_terms(const T Q[5], const T dq[3][5], S gm1, S K, bool pos, T q0[5], T b4[5],
                         T w5[5], T b5[5], T w6[5], T b6[5])
 {
     HalfSide<T> h;

@@ -16,6 +16,7 @@ struct hgks_s {
     int cur = 0;
     double *qs = nullptr, *r = nullptr;
     double *fq = nullptr, *t1 = nullptr;
+    double *qf = nullptr;  // mixed precision: the state split into hi / lo float planes
     double *F[3] = { nullptr, nullptr, nullptr };
     double *io[2] = { nullptr, nullptr };  // interior staging buffers [5][N]
     double *ytab = nullptr;                // y metric tables

@@ -63,7 +63,8 @@ void launch_flux(const Params &P, int d, const double *t1, double *F, const Ctl 
 void launch_wall(const Params &P, const double *Fy, Ctl *ctl, double lxlz, cudaStream_t st);
 // mixed-precision sweep passes (which: 0 normal, 1 first tangential, 2 flux),
 // using the same fq / t1 buffers as the FP64 passes
-void launch_sweep_mixed(const Params &P, int d, const double *q, double *fq, double *t1, double *F, const Ctl *ctl,
+void launch_split_mixed(const Params &P, const double *q, double *qf, const Ctl *ctl, cudaStream_t st);
+void launch_sweep_mixed(const Params &P, int d, const double *qf, double *fq, double *t1, double *F, const Ctl *ctl,
                         cudaStream_t st, int which);
 // stage 1: qs = q + dt/2 L + dt^2/8 dL, r = q + dt L + dt^2/6 dL;  stage 2: qn = r + dt^2/3 dL
 void launch_update(const Params &P, int stage, const double *q, const double *const F[3], double *out_a,

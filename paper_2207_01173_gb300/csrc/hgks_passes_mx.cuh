@@ -1,32 +1,38 @@
-// hgks_passes_mx.cuh -- the mixed-precision sweep passes (HGKS_MIXED): FP32 reconstruction
-// and flux arithmetic, FP64 state, equilibrium state and equilibrium flux.
+// hgks_passes_mx.cuh -- the mixed-precision sweep passes (HGKS_MIXED): FP32
+// reconstruction and flux arithmetic, FP64 state and update, float-float
+// (two-FP32, ~48-bit) values wherever FP32 alone would lose digits.
 //
-// Where FP64 stays, and why (low-Mach flows lose digits to cancellation):
-//   * cell averages, stage sums and the S2O4 update (the k_update kernel) --
-//     a step changes rho E by ~1e-6 of its value;
-//   * every reconstructed VALUE is an FP64 centre value plus an FP32
-//     deviation: WENO-Z and the quartics act on differences from the centre
-//     of their stencil, which are small and keep full FP32 relative
-//     precision (the nonlinear weights depend on differences only);
+// Where the extra precision stays, and why (low-Mach flows lose digits to
+// cancellation: a step changes rho E by ~1e-6 of its value, and the flux
+// differences of neighbouring faces cancel all but ~h/L of the flux):
+//   * cell averages, stage sums and the S2O4 update (k_update) -- FP64;
+//   * every reconstructed VALUE -- float-float.  Before each stage the state
+//     is split once into hi + lo FP32 planes (k_split_mx), so the passes need
+//     no FP64 instruction: WENO-Z and the quartics act on differences from
+//     the centre of their stencil, formed as (hi_j - hi_c) + (lo_j - lo_c),
+//     which keep full FP32 relative precision (the nonlinear weights depend
+//     on differences only), and a value is the centre pair plus that FP32
+//     deviation;
 //   * the equilibrium state Q0 = (Ql + Qr)/2 + C at each Gauss point: the
 //     compatibility correction C is small for smooth data and is evaluated in
 //     FP32 as -(DPhi+(Ql) - DPhi-(Qr))[Qr - Ql]/2 (trapezoidal rule for the
 //     difference of half-range moment functions whose sum is the identity;
 //     error O(|Qr - Ql|^3)), or directly as Phi+(Ql) + Phi-(Qr) when the jump
 //     is not small;
-//   * the temperature and pressure of Q0 and its Euler flux B1 = F_n(Q0),
-//     which carries the pressure whose face-to-face differences drive L.
+//   * the pressure of Q0 and its Euler flux B1 = F_n(Q0), whose face-to-face
+//     differences drive L -- float-float.
 // Everything else -- slopes, half-range moments, the collision time and the
 // non-equilibrium / time-derivative terms, all scaled by tau or dt -- is
 // FP32.  The flux becomes F^n = B1 + (4 S(dt/2) - S(dt))/dt and
 // dF^n/dt = 4 (S(dt) - 2 S(dt/2))/dt^2 with S the FP32 sum of the small
-// terms, because the B1 part of I(delta) is exactly delta B1.
+// terms, because the B1 part of I(delta) is exactly delta B1.  Only the final
+// face flux is converted to FP64 for the update.
 #pragma once
 #include "hgks_bodies.cuh"
+#include "hgks_ff.cuh"
 #include "hgks_kernels.cuh"
 
 namespace hgks {
-
 
 __host__ __device__ inline int perm_mx(int d, int c)
 {
@@ -53,129 +59,216 @@ static __device__ __forceinline__ long long bstride(const Box &b, int e)
 }
 
 // ---------------------------------------------------------------------------
-// equilibrium state from left/right states (FP64 values)
+// buffer views of the mixed passes (inside the FP64-sized handle buffers)
 // ---------------------------------------------------------------------------
-// Q0 = Qm + C; hl, hr: half-range setups of Ql (u > 0) and Qr (u < 0) in FP32
-static __device__ __forceinline__ void compat_mixed(const double Ql[5], const double Qr[5], const HalfSide<float> &hl,
-                                             const HalfSide<float> &hr, double gm1, double K, double Q0[5])
+// state split: qh[5][cs], ql[5][cs] floats
+// pass 1 (fq): vh[15][nq], vl[15][nq] (Ql, Qr, Q0 values), vs[15][nq] (dQl, dQr, dQ0 in index units)
+// pass 2 (t1), per Gauss line m: th[2][25][nt], tl[2][25][nt] (WENO values of Ql, Qr (10), quartic
+//   values of Ql, Qr, Q0 (15)), ts[2][30][nt] (WENO of the slopes (15), quartic derivatives (15))
+struct FqMx {
+    float *vh, *vl, *vs;
+};
+struct T1Mx {
+    float *th, *tl, *ts;
+};
+__host__ __device__ inline FqMx fq_mx(double *fq, long long nq)
 {
-    double Qm[5];
-    float dq[5];
+    float *f = (float *)fq;
+    return FqMx{ f, f + 15 * nq, f + 30 * nq };
+}
+__host__ __device__ inline T1Mx t1_mx(double *t1, long long nt)
+{
+    float *f = (float *)t1;
+    return T1Mx{ f, f + 50 * nt, f + 100 * nt };
+}
+
+// the state as hi + lo float planes
+static __device__ __forceinline__ void pos_split_mx(const Params &P, const double *__restrict__ q,
+                                                    float *__restrict__ qh, float *__restrict__ ql, long long t)
+{
 #pragma unroll
     for (int c = 0; c < 5; c++) {
-        Qm[c] = 0.5 * (Ql[c] + Qr[c]);
-        dq[c] = (float)(Qr[c] - Ql[c]);
+        const ff v = ff_of_double(q[c * P.cs + t]);
+        qh[c * P.cs + t] = v.hi;
+        ql[c * P.cs + t] = v.lo;
     }
-    const float jump = fabsf(dq[0]) / (float)Qm[0] + fabsf(dq[4]) / (float)Qm[4];
-    if (jump < 1e-3f) {
-        HalfDelta<float> d;
-        float a[5], b[5];
-        half_delta(hl, dq, gm1, K, d);
-        half_dphi<0, 0, 0>(hl, d, a);  // DPhi+(Ql)[dq]
-        half_delta(hr, dq, gm1, K, d);
-        half_dphi<0, 0, 0>(hr, d, b);  // DPhi-(Qr)[dq]
+}
+
+// stencil deviations x_j = X_j - X_c of float-float values
+static __device__ __forceinline__ float ff_dev(float hj, float lj, float hc, float lc) { return (hj - hc) + (lj - lc); }
+
+// the gas constants of the FP32 flux, held in registers (the batched kernels
+// read Params from global memory, so the point flux takes them by value)
+struct MxGas {
+    float gm1, gm1_lo, K, prc, mu_ref, inv_Tref, omega;
+    int power_law;
+};
+static __device__ __forceinline__ MxGas mx_gas(const Params &P)
+{
+    return MxGas{ P.f_gm1, P.f_gm1_lo, P.f_K, P.f_prc, P.f_mu_ref, P.f_inv_Tref, P.f_omega, P.visc_kind == 1 };
+}
+
+// FP32 viscosity law
+static __device__ __forceinline__ float viscosity_f(const MxGas &G, float Tm)
+{
+    return G.power_law ? G.mu_ref * powf(Tm * G.inv_Tref, G.omega) : G.mu_ref;
+}
+
+// ---------------------------------------------------------------------------
+// one side's half-range terms (FP32)
+// ---------------------------------------------------------------------------
+// For the side of Ql (POS: u > 0) or Qr (u < 0): the half-range flux b4, the
+// slope terms w5/b5 (the three spatial slopes dq), the time-slope terms w6/b6,
+// and the side's part of the compatibility condition: DPhi(q)[jq] when the
+// jump is small (trapezoidal form), else Phi(q) itself.  The two sides are
+// done one after the other so that only one side's moment set is live.
+template <bool POS>
+static __device__ __forceinline__ void side_terms_mx(const float q[5], const float dq[3][5], const float jq[5],
+                                                     bool small_jump, float gm1, float K, float b4[5], float w5[5],
+                                                     float b5[5], float w6[5], float b6[5], float cp[5])
+{
+    HalfSide<float> h;
+    half_side_setup(q, gm1, K, POS, h);
+    HalfDelta<float> dd;
+    float s[5];
+    half_phi<1, 0, 0>(h, b4);
+    half_delta(h, dq[0], gm1, K, dd);
+    half_dphi<1, 0, 0>(h, dd, w5);
+    half_dphi<2, 0, 0>(h, dd, b5);
+    half_delta(h, dq[1], gm1, K, dd);
+    half_dphi<0, 1, 0>(h, dd, s);
 #pragma unroll
-        for (int c = 0; c < 5; c++) Q0[c] = Qm[c] - 0.5 * (double)(a[c] - b[c]);
+    for (int c = 0; c < 5; c++) w5[c] += s[c];
+    half_dphi<1, 1, 0>(h, dd, s);
+#pragma unroll
+    for (int c = 0; c < 5; c++) b5[c] += s[c];
+    half_delta(h, dq[2], gm1, K, dd);
+    half_dphi<0, 0, 1>(h, dd, s);
+#pragma unroll
+    for (int c = 0; c < 5; c++) w5[c] += s[c];
+    half_dphi<1, 0, 1>(h, dd, s);
+#pragma unroll
+    for (int c = 0; c < 5; c++) b5[c] += s[c];
+    // time slope of the side
+    const Gas<float> g = gas_of(q, gm1);
+    float tq[5];
+    euler_dtq(g, dq, gm1, tq);
+    half_delta(h, tq, gm1, K, dd);
+    half_dphi<0, 0, 0>(h, dd, w6);
+    half_dphi<1, 0, 0>(h, dd, b6);
+    if (small_jump) {
+        half_delta(h, jq, gm1, K, dd);
+        half_dphi<0, 0, 0>(h, dd, cp);
     } else {
-        float a[5], b[5];
-        half_phi<0, 0, 0>(hl, a);
-        half_phi<0, 0, 0>(hr, b);
-#pragma unroll
-        for (int c = 0; c < 5; c++) Q0[c] = (double)a[c] + (double)b[c];
+        half_phi<0, 0, 0>(h, cp);
     }
+}
+
+// Q0 = Qm + C from the two sides' compatibility parts: with a small jump
+// C = -(DPhi+(Ql) - DPhi-(Qr))[Qr - Ql] / 2, else Q0 = Phi+(Ql) + Phi-(Qr)
+static __device__ __forceinline__ bool compat_prepare(const ff Ql[5], const ff Qr[5], ff Qm[5], float dq[5])
+{
+#pragma unroll
+    for (int c = 0; c < 5; c++) {
+        Qm[c] = ff_scale(ff_add(Ql[c], Qr[c]), 0.5f);
+        dq[c] = ff_dev(Qr[c].hi, Qr[c].lo, Ql[c].hi, Ql[c].lo);
+    }
+    return fabsf(dq[0]) / Qm[0].hi + fabsf(dq[4]) / Qm[4].hi < 1e-3f;
+}
+static __device__ __forceinline__ void compat_finish(bool small_jump, const ff Qm[5], const float cl[5],
+                                                     const float cr[5], ff Q0[5])
+{
+#pragma unroll
+    for (int c = 0; c < 5; c++)
+        Q0[c] = small_jump ? ff_add_f(Qm[c], -0.5f * (cl[c] - cr[c])) : ff_two_sum(cl[c], cr[c]);
+}
+
+// the equilibrium state alone (pass 1): both sides' compatibility parts
+static __device__ __forceinline__ void compat_mixed(const ff Ql[5], const ff Qr[5], float gm1, float K, ff Q0[5])
+{
+    ff Qm[5];
+    float dq[5], cl[5], cr[5];
+    const bool small_jump = compat_prepare(Ql, Qr, Qm, dq);
+    float q[5];
+    {
+#pragma unroll
+        for (int c = 0; c < 5; c++) q[c] = ff_to_float(Ql[c]);
+        HalfSide<float> h;
+        half_side_setup(q, gm1, K, true, h);
+        if (small_jump) {
+            HalfDelta<float> dd;
+            half_delta(h, dq, gm1, K, dd);
+            half_dphi<0, 0, 0>(h, dd, cl);
+        } else {
+            half_phi<0, 0, 0>(h, cl);
+        }
+    }
+    {
+#pragma unroll
+        for (int c = 0; c < 5; c++) q[c] = ff_to_float(Qr[c]);
+        HalfSide<float> h;
+        half_side_setup(q, gm1, K, false, h);
+        if (small_jump) {
+            HalfDelta<float> dd;
+            half_delta(h, dq, gm1, K, dd);
+            half_dphi<0, 0, 0>(h, dd, cr);
+        } else {
+            half_phi<0, 0, 0>(h, cr);
+        }
+    }
+    compat_finish(small_jump, Qm, cl, cr, Q0);
 }
 
 // ---------------------------------------------------------------------------
 // Gauss-point flux, mixed precision
 // ---------------------------------------------------------------------------
-static __device__ __noinline__ void gks_point_flux_mixed(const double Ql[5], const double Qr[5], const float dl[3][5],
-                                                  const float dr[3][5], const float d0[3][5], const Params &P,
-                                                  double dt, double Fn[5], double dFn[5])
+static __device__ __noinline__ void gks_point_flux_mixed(const ff Ql[5], const ff Qr[5], const float dl[3][5],
+                                                         const float dr[3][5], const float d0[3][5],
+                                                         const MxGas G, float dtf, ff Fn[5], float dFn[5])
 {
-    const double gm1 = P.gamma - 1.0, K = P.K;
-    float qlf[5], qrf[5];
-#pragma unroll
-    for (int c = 0; c < 5; c++) {
-        qlf[c] = (float)Ql[c];
-        qrf[c] = (float)Qr[c];
-    }
-    // half-range terms of the two sides (FP32)
-    HalfSide<float> hl, hr;
-    half_side_setup(qlf, gm1, K, true, hl);
-    half_side_setup(qrf, gm1, K, false, hr);
-    float b4l[5], w5l[5], b5l[5], w6l[5], b6l[5], b4r[5], w5r[5], b5r[5], w6r[5], b6r[5];
+    const float gm1 = G.gm1, K = G.K;
+    ff Qm[5];
+    float jq[5];
+    const bool small_jump = compat_prepare(Ql, Qr, Qm, jq);
+    // half-range terms of the two sides (FP32), one side at a time
+    float b4l[5], w5l[5], b5l[5], w6l[5], b6l[5], b4r[5], w5r[5], b5r[5], w6r[5], b6r[5], cl[5], cr[5];
     {
-        HalfDelta<float> dd;
-        float s[5];
-        half_phi<1, 0, 0>(hl, b4l);
-        half_phi<1, 0, 0>(hr, b4r);
-        half_delta(hl, dl[0], gm1, K, dd);
-        half_dphi<1, 0, 0>(hl, dd, w5l);
-        half_dphi<2, 0, 0>(hl, dd, b5l);
-        half_delta(hl, dl[1], gm1, K, dd);
-        half_dphi<0, 1, 0>(hl, dd, s);
+        float q[5];
 #pragma unroll
-        for (int c = 0; c < 5; c++) w5l[c] += s[c];
-        half_dphi<1, 1, 0>(hl, dd, s);
+        for (int c = 0; c < 5; c++) q[c] = ff_to_float(Ql[c]);
+        side_terms_mx<true>(q, dl, jq, small_jump, gm1, K, b4l, w5l, b5l, w6l, b6l, cl);
+    }
+    {
+        float q[5];
 #pragma unroll
-        for (int c = 0; c < 5; c++) b5l[c] += s[c];
-        half_delta(hl, dl[2], gm1, K, dd);
-        half_dphi<0, 0, 1>(hl, dd, s);
-#pragma unroll
-        for (int c = 0; c < 5; c++) w5l[c] += s[c];
-        half_dphi<1, 0, 1>(hl, dd, s);
-#pragma unroll
-        for (int c = 0; c < 5; c++) b5l[c] += s[c];
-        half_delta(hr, dr[0], gm1, K, dd);
-        half_dphi<1, 0, 0>(hr, dd, w5r);
-        half_dphi<2, 0, 0>(hr, dd, b5r);
-        half_delta(hr, dr[1], gm1, K, dd);
-        half_dphi<0, 1, 0>(hr, dd, s);
-#pragma unroll
-        for (int c = 0; c < 5; c++) w5r[c] += s[c];
-        half_dphi<1, 1, 0>(hr, dd, s);
-#pragma unroll
-        for (int c = 0; c < 5; c++) b5r[c] += s[c];
-        half_delta(hr, dr[2], gm1, K, dd);
-        half_dphi<0, 0, 1>(hr, dd, s);
-#pragma unroll
-        for (int c = 0; c < 5; c++) w5r[c] += s[c];
-        half_dphi<1, 0, 1>(hr, dd, s);
-#pragma unroll
-        for (int c = 0; c < 5; c++) b5r[c] += s[c];
-        // time slopes of the two sides
-        const Gas<float> gl = gas_of(qlf, gm1), gr = gas_of(qrf, gm1);
-        float tq[5];
-        euler_dtq(gl, dl, gm1, tq);
-        half_delta(hl, tq, gm1, K, dd);
-        half_dphi<0, 0, 0>(hl, dd, w6l);
-        half_dphi<1, 0, 0>(hl, dd, b6l);
-        euler_dtq(gr, dr, gm1, tq);
-        half_delta(hr, tq, gm1, K, dd);
-        half_dphi<0, 0, 0>(hr, dd, w6r);
-        half_dphi<1, 0, 0>(hr, dd, b6r);
+        for (int c = 0; c < 5; c++) q[c] = ff_to_float(Qr[c]);
+        side_terms_mx<false>(q, dr, jq, small_jump, gm1, K, b4r, w5r, b5r, w6r, b6r, cr);
     }
 
-    // equilibrium state and its Euler flux in FP64
-    double Q0[5];
-    compat_mixed(Ql, Qr, hl, hr, gm1, K, Q0);
-    const double ir0 = 1.0 / Q0[0];
-    const double U0 = Q0[1] * ir0, V0 = Q0[2] * ir0, W0 = Q0[3] * ir0;
-    const double p0 = gm1 * (Q0[4] - 0.5 * Q0[0] * (U0 * U0 + V0 * V0 + W0 * W0));
-    double B1[5];
+    // equilibrium state and its Euler flux in float-float
+    ff Q0[5];
+    compat_finish(small_jump, Qm, cl, cr, Q0);
+    const ff gm1ff{ G.gm1, G.gm1_lo };
+    const ff ir0 = ff_recip(Q0[0]);
+    const ff U0 = ff_mul(Q0[1], ir0), V0 = ff_mul(Q0[2], ir0), W0 = ff_mul(Q0[3], ir0);
+    const ff mU = ff_mul(Q0[1], U0);  // rho U^2
+    const ff m2 = ff_add(ff_add(mU, ff_mul(Q0[2], V0)), ff_mul(Q0[3], W0));
+    const ff p0 = ff_mul(gm1ff, ff_sub(Q0[4], ff_scale(m2, 0.5f)));
+    ff B1[5];
     B1[0] = Q0[1];
-    B1[1] = Q0[1] * U0 + p0;
-    B1[2] = Q0[1] * V0;
-    B1[3] = Q0[1] * W0;
-    B1[4] = U0 * (Q0[4] + p0);
+    B1[1] = ff_add(mU, p0);
+    B1[2] = ff_mul(Q0[1], V0);
+    B1[3] = ff_mul(Q0[1], W0);
+    B1[4] = ff_mul(U0, ff_add(Q0[4], p0));
 
     // FP32: equilibrium slope terms, collision time, the small terms S(delta)
     float q0f[5];
 #pragma unroll
-    for (int c = 0; c < 5; c++) q0f[c] = (float)Q0[c];
+    for (int c = 0; c < 5; c++) q0f[c] = ff_to_float(Q0[c]);
     const Gas<float> g0 = gas_of(q0f, gm1);
-    const float T0 = (float)(p0 * ir0);
-    const float tau = viscosity(P, T0) / (float)p0;
+    const float p0f = ff_to_float(p0);
+    const float T0 = p0f * ff_to_float(ir0);
+    const float tau = viscosity_f(G, T0) / p0f;
     float B2[5], B3[5], R0[5], B4m1[5], W5[5], B5[5], W6[5], B6[5];
     {
         float s[5];
@@ -190,16 +283,18 @@ static __device__ __noinline__ void gks_point_flux_mixed(const double Ql[5], con
 #pragma unroll
         for (int c = 0; c < 5; c++) dtQ0[c] = -R0[c];
         euler_dflux<0>(g0, dtQ0, gm1, B3);
-        second_dmoment<0>(g0, d0[0], gm1, K + 5.0, B2);
-        second_dmoment<1>(g0, d0[1], gm1, K + 5.0, s);
+        const float Kp5 = K + 5.0f;
+        second_dmoment<0>(g0, d0[0], gm1, Kp5, B2);
+        second_dmoment<1>(g0, d0[1], gm1, Kp5, s);
 #pragma unroll
         for (int c = 0; c < 5; c++) B2[c] += s[c];
-        second_dmoment<2>(g0, d0[2], gm1, K + 5.0, s);
+        second_dmoment<2>(g0, d0[2], gm1, Kp5, s);
 #pragma unroll
         for (int c = 0; c < 5; c++) B2[c] += s[c];
 #pragma unroll
         for (int c = 0; c < 5; c++) {
-            B4m1[c] = (b4l[c] + b4r[c]) - (float)B1[c];  // half-range flux minus the equilibrium flux
+            // half-range flux minus the equilibrium flux
+            B4m1[c] = ff_to_float(ff_sub(ff_two_sum(b4l[c], b4r[c]), B1[c]));
             W5[c] = w5l[c] + w5r[c];
             B5[c] = b5l[c] + b5r[c];
             W6[c] = w6l[c] + w6r[c];
@@ -208,17 +303,15 @@ static __device__ __noinline__ void gks_point_flux_mixed(const double Ql[5], con
     }
     // heat fluxes of the terms (the equilibrium carries none; the B4 - B1 term
     // carries that of the half-range part: h(B4, Q0) - h(B1, Q0) = h(B4, Q0))
-    float W3[5], Q0f[5], b4s[5];
+    float W3[5], b4s[5];
 #pragma unroll
     for (int c = 0; c < 5; c++) {
         W3[c] = -R0[c];
-        Q0f[c] = q0f[c];
         b4s[c] = b4l[c] + b4r[c];
     }
-    const float h2 = heat_of_g(B2, R0, g0), h3 = heat_of_g(B3, W3, g0), h4 = heat_of_g(b4s, Q0f, g0),
+    const float h2 = heat_of_g(B2, R0, g0), h3 = heat_of_g(B3, W3, g0), h4 = heat_of_g(b4s, q0f, g0),
                 h5 = heat_of_g(B5, W5, g0), h6 = heat_of_g(B6, W6, g0);
-    const float prc = (float)(1.0 / P.Pr - 1.0);
-    const float dtf = (float)dt;
+    const float prc = G.prc;
     const float eh = tau > 0.0f ? expf(-0.5f * dtf / tau) : 0.0f;
     float S[2][5];
 #pragma unroll
@@ -239,18 +332,17 @@ static __device__ __noinline__ void gks_point_flux_mixed(const double Ql[5], con
     const float idt = 1.0f / dtf;
 #pragma unroll
     for (int i = 0; i < 5; i++) {
-        Fn[i] = B1[i] + (double)((4.0f * S[1][i] - S[0][i]) * idt);
-        dFn[i] = (double)(4.0f * (S[0][i] - 2.0f * S[1][i]) * idt * idt);
+        Fn[i] = ff_add_f(B1[i], (4.0f * S[1][i] - S[0][i]) * idt);
+        dFn[i] = 4.0f * (S[0][i] - 2.0f * S[1][i]) * idt * idt;
     }
 }
 
 // ---------------------------------------------------------------------------
-// pass 1: normal reconstruction (values FP64 = centre + FP32 deviation)
+// pass 1: normal reconstruction from the split state
 // ---------------------------------------------------------------------------
-// fqd[15][nq] doubles: Ql, Qr, Q0 values; fqf[15][nq] floats: dQl, dQr, dQ0 (index units)
 static __device__ __forceinline__ void pos_normal_mx(const Params &P, int d, const Box &B,
-                                                     const double *__restrict__ q, double *__restrict__ fqd,
-                                                     float *__restrict__ fqf, long long t)
+                                                     const float *__restrict__ qh, const float *__restrict__ ql,
+                                                     FqMx o, long long t)
 {
     const long long nq = box_count(B);
     int p[3];
@@ -259,18 +351,21 @@ static __device__ __forceinline__ void pos_normal_mx(const Params &P, int d, con
     c0[d] = p[d] - 3;
     const long long base = pidx(P, c0[0], c0[1], c0[2]);
     const long long sd = d == 0 ? 1 : (d == 1 ? P.sy : P.sz);
-    double Ql[5], Qr[5];
+    ff Ql[5], Qr[5];
 #pragma unroll
     for (int c = 0; c < 5; c++) {
-        const double *src = q + (long long)perm_mx(d, c) * P.cs + base;
-        double X[6];
+        const long long off = (long long)perm_mx(d, c) * P.cs + base;
+        float H[6], L[6];
 #pragma unroll
-        for (int m = 0; m < 6; m++) X[m] = src[m * sd];
+        for (int m = 0; m < 6; m++) {
+            H[m] = qh[off + m * sd];
+            L[m] = ql[off + m * sd];
+        }
         float xl[5], xr[5];
 #pragma unroll
         for (int m = 0; m < 5; m++) {
-            xl[m] = (float)(X[m] - X[2]);      // cell f-1 stencil, about its centre
-            xr[m] = (float)(X[m + 1] - X[3]);  // cell f stencil
+            xl[m] = ff_dev(H[m], L[m], H[2], L[2]);          // cell f-1 stencil, about its centre
+            xr[m] = ff_dev(H[m + 1], L[m + 1], H[3], L[3]);  // cell f stencil
         }
         WenoPrep<float> wl, wr;
         weno_prep(xl, wl);
@@ -278,40 +373,32 @@ static __device__ __forceinline__ void pos_normal_mx(const Params &P, int d, con
         float lm_l, lm_r, r_l, r_r;
         weno_edge_pair(wl, lm_l, lm_r);
         weno_edge_pair(wr, r_l, r_r);
-        Ql[c] = X[2] + (double)lm_r;
-        Qr[c] = X[3] + (double)r_l;
-        fqd[(0 * 5 + c) * nq + t] = Ql[c];
-        fqd[(1 * 5 + c) * nq + t] = Qr[c];
-        fqf[(0 * 5 + c) * nq + t] = 2.0f * lm_l + 4.0f * lm_r;  // parabola slopes (centre cancels)
-        fqf[(1 * 5 + c) * nq + t] = -4.0f * r_l - 2.0f * r_r;
-        fqf[(2 * 5 + c) * nq + t] = (15.0f * (float)(X[3] - X[2]) - (float)(X[4] - X[1])) * (1.0f / 12.0f);
+        Ql[c] = ff_add_f(ff{ H[2], L[2] }, lm_r);
+        Qr[c] = ff_add_f(ff{ H[3], L[3] }, r_l);
+        o.vh[(0 * 5 + c) * nq + t] = Ql[c].hi;
+        o.vl[(0 * 5 + c) * nq + t] = Ql[c].lo;
+        o.vh[(1 * 5 + c) * nq + t] = Qr[c].hi;
+        o.vl[(1 * 5 + c) * nq + t] = Qr[c].lo;
+        o.vs[(0 * 5 + c) * nq + t] = 2.0f * lm_l + 4.0f * lm_r;  // parabola slopes (centre cancels)
+        o.vs[(1 * 5 + c) * nq + t] = -4.0f * r_l - 2.0f * r_r;
+        o.vs[(2 * 5 + c) * nq + t] = (15.0f * xl[3] - (xl[4] - xl[1])) * (1.0f / 12.0f);
     }
-    float qlf[5], qrf[5];
+    ff Q0[5];
+    compat_mixed(Ql, Qr, P.f_gm1, P.f_K, Q0);
 #pragma unroll
     for (int c = 0; c < 5; c++) {
-        qlf[c] = (float)Ql[c];
-        qrf[c] = (float)Qr[c];
+        o.vh[(2 * 5 + c) * nq + t] = Q0[c].hi;
+        o.vl[(2 * 5 + c) * nq + t] = Q0[c].lo;
     }
-    HalfSide<float> hl, hr;
-    half_side_setup(qlf, P.gamma - 1.0, P.K, true, hl);
-    half_side_setup(qrf, P.gamma - 1.0, P.K, false, hr);
-    double Q0[5];
-    compat_mixed(Ql, Qr, hl, hr, P.gamma - 1.0, P.K, Q0);
-#pragma unroll
-    for (int c = 0; c < 5; c++) fqd[(2 * 5 + c) * nq + t] = Q0[c];
 }
 
 // ---------------------------------------------------------------------------
 // pass 2: first tangential direction
 // ---------------------------------------------------------------------------
-// t1d[2][25][nt] doubles per Gauss line m: WENO values of Ql, Qr (10), quartic
-// values of Ql, Qr, Q0 (15); t1f[2][30][nt] floats: WENO of dQl, dQr, dQ0 (15),
-// quartic derivatives of Ql, Qr, Q0 (15)
-static __device__ __forceinline__ void pos_tan1_mx(const Params &P, int d, const Box &Bt, const Box &Bq,
-                                                   const double *__restrict__ fqd, const float *__restrict__ fqf,
-                                                   double *__restrict__ t1d, float *__restrict__ t1f, long long t)
+static __device__ __forceinline__ void pos_tan1_mx(const Params &P, int d, const Box &Bt, const Box &Bq, FqMx in,
+                                                   T1Mx o, long long t)
 {
-    const long long nt = box_count(Bt), nq = box_count(Bq);
+    const long long nt = box_count(Bt);
     int p[3];
     bpos(Bt, t, p);
     const long long base = blin(Bq, p), s1 = bstride(Bq, tdir(d, 0));
@@ -320,28 +407,37 @@ static __device__ __forceinline__ void pos_tan1_mx(const Params &P, int d, const
     for (int v = 0; v < 3; v++) {
 #pragma unroll
         for (int c = 0; c < 5; c++) {
-            const double *src = fqd + (v * 5 + c) * nq + base;
-            double X[5];
+            const long long off = (long long)(v * 5 + c) * box_count(Bq) + base;
+            float H[5], L[5], x[5];
 #pragma unroll
-            for (int j = 0; j < 5; j++) X[j] = src[(j - 2) * s1];
-            float x[5];
+            for (int j = 0; j < 5; j++) {
+                H[j] = in.vh[off + (j - 2) * s1];
+                L[j] = in.vl[off + (j - 2) * s1];
+            }
 #pragma unroll
-            for (int j = 0; j < 5; j++) x[j] = (float)(X[j] - X[2]);
+            for (int j = 0; j < 5; j++) x[j] = ff_dev(H[j], L[j], H[2], L[2]);
+            const ff ctr{ H[2], L[2] };
             if (v < 2) {
                 WenoPrep<float> W;
                 weno_prep(x, W);
                 float vm, vp;
                 weno_gauss_pair(W, vm, vp);
-                t1d[(0 * 25 + v * 5 + c) * nt + t] = X[2] + (double)vm;
-                t1d[(1 * 25 + v * 5 + c) * nt + t] = X[2] + (double)vp;
+                const ff am = ff_add_f(ctr, vm), ap = ff_add_f(ctr, vp);
+                o.th[(0 * 25 + v * 5 + c) * nt + t] = am.hi;
+                o.tl[(0 * 25 + v * 5 + c) * nt + t] = am.lo;
+                o.th[(1 * 25 + v * 5 + c) * nt + t] = ap.hi;
+                o.tl[(1 * 25 + v * 5 + c) * nt + t] = ap.lo;
             }
             float qm, qp, dm, dp;
             quartic_value_pair(x, qm, qp);
             quartic_deriv_pair(x, dm, dp);
-            t1d[(0 * 25 + 10 + v * 5 + c) * nt + t] = X[2] + (double)qm;
-            t1d[(1 * 25 + 10 + v * 5 + c) * nt + t] = X[2] + (double)qp;
-            t1f[(0 * 30 + 15 + v * 5 + c) * nt + t] = dm;
-            t1f[(1 * 30 + 15 + v * 5 + c) * nt + t] = dp;
+            const ff bm = ff_add_f(ctr, qm), bp = ff_add_f(ctr, qp);
+            o.th[(0 * 25 + 10 + v * 5 + c) * nt + t] = bm.hi;
+            o.tl[(0 * 25 + 10 + v * 5 + c) * nt + t] = bm.lo;
+            o.th[(1 * 25 + 10 + v * 5 + c) * nt + t] = bp.hi;
+            o.tl[(1 * 25 + 10 + v * 5 + c) * nt + t] = bp.lo;
+            o.ts[(0 * 30 + 15 + v * 5 + c) * nt + t] = dm;
+            o.ts[(1 * 30 + 15 + v * 5 + c) * nt + t] = dp;
         }
     }
     // slopes: WENO-Z in FP32
@@ -349,7 +445,7 @@ static __device__ __forceinline__ void pos_tan1_mx(const Params &P, int d, const
     for (int w = 0; w < 3; w++) {
 #pragma unroll
         for (int c = 0; c < 5; c++) {
-            const float *src = fqf + (w * 5 + c) * nq + base;
+            const float *src = in.vs + (long long)(w * 5 + c) * box_count(Bq) + base;
             float x[5];
 #pragma unroll
             for (int j = 0; j < 5; j++) x[j] = src[(j - 2) * s1];
@@ -357,8 +453,8 @@ static __device__ __forceinline__ void pos_tan1_mx(const Params &P, int d, const
             weno_prep(x, W);
             float vm, vp;
             weno_gauss_pair(W, vm, vp);
-            t1f[(0 * 30 + w * 5 + c) * nt + t] = vm;
-            t1f[(1 * 30 + w * 5 + c) * nt + t] = vp;
+            o.ts[(0 * 30 + w * 5 + c) * nt + t] = vm;
+            o.ts[(1 * 30 + w * 5 + c) * nt + t] = vp;
         }
     }
 }
@@ -366,8 +462,12 @@ static __device__ __forceinline__ void pos_tan1_mx(const Params &P, int d, const
 // ---------------------------------------------------------------------------
 // pass 3: second tangential direction and the four Gauss-point fluxes
 // ---------------------------------------------------------------------------
-static __device__ __forceinline__ void pos_flux_mx(const Params &P, int d, const Box &Bf, const Box &Bt,
-                                                   const double *__restrict__ t1d, const float *__restrict__ t1f,
+static __device__ __forceinline__ float inv_metric_f(const Params &P, int e, const double *tab, int idx)
+{
+    return e == 1 && P.stretched ? 1.0f / (float)tab[idx] : P.f_ih[e];
+}
+
+static __device__ __forceinline__ void pos_flux_mx(const Params &P, int d, const Box &Bf, const Box &Bt, T1Mx in,
                                                    double *__restrict__ F, double dt, long long t)
 {
     const long long nf = box_count(Bf), nt = box_count(Bt);
@@ -376,52 +476,60 @@ static __device__ __forceinline__ void pos_flux_mx(const Params &P, int d, const
     const int e1 = tdir(d, 0), e2 = tdir(d, 1);
     const int f = p[d], a = p[e1], b = p[e2];
     const long long base = blin(Bt, p), s2 = bstride(Bt, e2);
-    const float ihn = (float)(1.0 / (d == 1 ? P.my_face[f] : P.h[d]));
-    double area;
-    if (d == 0) area = P.hy_cell[a] * P.h[2];
-    else if (d == 1) area = P.h[0] * P.h[2];
-    else area = P.h[0] * P.hy_cell[b];
+    const float ihn = inv_metric_f(P, d, P.my_face, f);
+    const float dtf = (float)dt;
+    const MxGas G = mx_gas(P);
 
-    double Fs[5] = { 0, 0, 0, 0, 0 }, dFs[5] = { 0, 0, 0, 0, 0 };
+    ff Fs[5];
+    float dFs[5];
+#pragma unroll
+    for (int c = 0; c < 5; c++) {
+        Fs[c] = ff{ 0.0f, 0.0f };
+        dFs[c] = 0.0f;
+    }
 #pragma unroll 1
     for (int m = 0; m < 2; m++) {
-        const float ih1 = (float)(1.0 / (e1 == 1 ? P.my_gp[2 * a + m] : P.h[e1]));
-        double gq[2][10];
+        const float ih1 = inv_metric_f(P, e1, P.my_gp, 2 * a + m);
+        ff gq[2][10];
         float gs[2][15], gd1[2][15], gd2[2][15];
         // values Ql, Qr at the two Gauss points of this line
 #pragma unroll 1
         for (int k = 0; k < 10; k++) {
-            const double *src = t1d + (m * 25 + k) * nt + base;
-            double X[5];
+            const long long off = (long long)(m * 25 + k) * nt + base;
+            float H[5], L[5], x[5];
 #pragma unroll
-            for (int j = 0; j < 5; j++) X[j] = src[(j - 2) * s2];
-            float x[5];
+            for (int j = 0; j < 5; j++) {
+                H[j] = in.th[off + (j - 2) * s2];
+                L[j] = in.tl[off + (j - 2) * s2];
+            }
 #pragma unroll
-            for (int j = 0; j < 5; j++) x[j] = (float)(X[j] - X[2]);
+            for (int j = 0; j < 5; j++) x[j] = ff_dev(H[j], L[j], H[2], L[2]);
             WenoPrep<float> W;
             weno_prep(x, W);
             float vm, vp;
             weno_gauss_pair(W, vm, vp);
-            gq[0][k] = X[2] + (double)vm;
-            gq[1][k] = X[2] + (double)vp;
+            gq[0][k] = ff_add_f(ff{ H[2], L[2] }, vm);
+            gq[1][k] = ff_add_f(ff{ H[2], L[2] }, vp);
         }
         // derivatives along the second tangential direction of the quartic values
 #pragma unroll 1
         for (int k = 0; k < 15; k++) {
-            const double *src = t1d + (m * 25 + 10 + k) * nt + base;
-            double X[5];
+            const long long off = (long long)(m * 25 + 10 + k) * nt + base;
+            float H[5], L[5], x[5];
 #pragma unroll
-            for (int j = 0; j < 5; j++) X[j] = src[(j - 2) * s2];
-            float x[5];
+            for (int j = 0; j < 5; j++) {
+                H[j] = in.th[off + (j - 2) * s2];
+                L[j] = in.tl[off + (j - 2) * s2];
+            }
 #pragma unroll
-            for (int j = 0; j < 5; j++) x[j] = (float)(X[j] - X[2]);
+            for (int j = 0; j < 5; j++) x[j] = ff_dev(H[j], L[j], H[2], L[2]);
             quartic_deriv_pair(x, gd2[0][k], gd2[1][k]);
         }
         // normal slopes (WENO) and first-direction derivatives (quartic value)
 #pragma unroll 1
         for (int k = 0; k < 15; k++) {
-            const float *ss = t1f + (m * 30 + k) * nt + base;
-            const float *sd = t1f + (m * 30 + 15 + k) * nt + base;
+            const float *ss = in.ts + (long long)(m * 30 + k) * nt + base;
+            const float *sd = in.ts + (long long)(m * 30 + 15 + k) * nt + base;
             float x[5], y[5];
 #pragma unroll
             for (int j = 0; j < 5; j++) {
@@ -435,7 +543,7 @@ static __device__ __forceinline__ void pos_flux_mx(const Params &P, int d, const
         }
 #pragma unroll 1
         for (int n = 0; n < 2; n++) {
-            const float ih2 = (float)(1.0 / (e2 == 1 ? P.my_gp[2 * b + n] : P.h[e2]));
+            const float ih2 = inv_metric_f(P, e2, P.my_gp, 2 * b + n);
             float dl[3][5], dr[3][5], d0[3][5];
 #pragma unroll
             for (int c = 0; c < 5; c++) {
@@ -449,19 +557,24 @@ static __device__ __forceinline__ void pos_flux_mx(const Params &P, int d, const
                 dr[2][c] = gd2[n][5 + c] * ih2;
                 d0[2][c] = gd2[n][10 + c] * ih2;
             }
-            double Fn[5], dFn[5];
-            gks_point_flux_mixed(&gq[n][0], &gq[n][5], dl, dr, d0, P, dt, Fn, dFn);
+            ff Fn[5];
+            float dFn[5];
+            gks_point_flux_mixed(&gq[n][0], &gq[n][5], dl, dr, d0, G, dtf, Fn, dFn);
 #pragma unroll
             for (int c = 0; c < 5; c++) {
-                Fs[c] += 0.25 * Fn[c];
-                dFs[c] += 0.25 * dFn[c];
+                Fs[c] = ff_add(Fs[c], ff_scale(Fn[c], 0.25f));  // Gauss weights 1/4 (exact)
+                dFs[c] += 0.25f * dFn[c];
             }
         }
     }
+    double area;
+    if (d == 0) area = P.hy_cell[a] * P.h[2];
+    else if (d == 1) area = P.h[0] * P.h[2];
+    else area = P.h[0] * P.hy_cell[b];
 #pragma unroll
     for (int c = 0; c < 5; c++) {
-        F[(long long)perm_mx(d, c) * nf + t] = Fs[c] * area;
-        F[(long long)(5 + perm_mx(d, c)) * nf + t] = dFs[c] * area;
+        F[(long long)perm_mx(d, c) * nf + t] = ff_to_double(Fs[c]) * area;
+        F[(long long)(5 + perm_mx(d, c)) * nf + t] = (double)dFs[c] * area;
     }
 }
 

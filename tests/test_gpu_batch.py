@@ -117,7 +117,7 @@ def test_batch_of_the_uneven_workload(hg):
     b.step(3, 0.5)
     info = b.info()
     assert info["last_steps"] == 3 and info["last_ms"] > 0.0
-    assert info["launches_per_step"] == 12 + 36
+    assert info["launches_per_step"] == 12 + 36 + 2
     for s1, s2 in zip(single, batched):
         assert np.array_equal(s1.get_state(), s2.get_state())
     b.close()
