@@ -158,18 +158,19 @@ __global__ void __launch_bounds__(128, MX ? 4 : 1) kb_tan1(const Inst *__restric
 // hardware block scheduler hands out the tiles.  A persistent loop keeps its
 // state live across the flux, which at the 128-register budget of this
 // latency-bound kernel raised the spills from 48 to 232 bytes and cost 40 %.
-constexpr int FLUX_MX_TILE = 128;
+constexpr int FLUX_MX_TILE = FLUX_MX_BLOCK;
 
-__global__ void __launch_bounds__(FLUX_MX_TILE, 4) kb_flux_mx(const Inst *__restrict__ I,
+__global__ void __launch_bounds__(FLUX_MX_TILE, 3) kb_flux_mx(const Inst *__restrict__ I,
                                                               const Tile *__restrict__ T, int ntiles, int d)
 {
+    extern __shared__ float gp_sm[];
     const int k = blockIdx.x;
     if (k >= ntiles) return;
     const Tile tl = T[k];
     const Inst &in = I[tl.inst];
     if (in.ctl->flag || (long long)threadIdx.x >= tl.count) return;
     const Box Bf = box_face(in.P, d), Bt = box_t1(in.P, d);
-    pos_flux_mx(in.P, d, Bf, Bt, t1_mx(in.t1, box_count(Bt)), in.F[d], in.ctl->dt, tl.start + threadIdx.x);
+    pos_flux_mx(in.P, d, Bf, Bt, t1_mx(in.t1, box_count(Bt)), in.F[d], in.ctl->dt, tl.start + threadIdx.x, gp_sm);
 }
 
 __global__ void __launch_bounds__(128) kb_flux(const Inst *__restrict__ I, const Tile *__restrict__ T, int ntiles,
@@ -352,7 +353,7 @@ static void enqueue_batch_step(hgks_batch_t b, double cfl)
                     kb_normal<true><<<pgrid(b->cnt[wn], b->bsweep[1][0]), 128, 0, st>>>(I, T(wn), b->cnt[wn], d,
                                                                                        stage);
                     kb_tan1<true><<<pgrid(b->cnt[wt], b->bsweep[1][1]), 128, 0, st>>>(I, T(wt), b->cnt[wt], d);
-                    kb_flux_mx<<<(unsigned)b->cnt[wf], FLUX_MX_TILE, 0, st>>>(I, T(wf), b->cnt[wf], d);
+                    kb_flux_mx<<<(unsigned)b->cnt[wf], FLUX_MX_TILE, FLUX_MX_SMEM, st>>>(I, T(wf), b->cnt[wf], d);
                 } else {
                     kb_normal<false><<<pgrid(b->cnt[wn], b->bsweep[0][0]), 128, 0, st>>>(I, T(wn), b->cnt[wn], d,
                                                                                         stage);
@@ -436,7 +437,8 @@ extern "C" hgks_status hgks_batch_create(hgks_t *handles, int n, hgks_batch_t *o
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[0][2], kb_flux, 128, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[1][0], kb_normal<true>, 128, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[1][1], kb_tan1<true>, 128, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[1][2], kb_flux_mx, FLUX_MX_TILE, 0);
+    cudaFuncSetAttribute((const void *)kb_flux_mx, cudaFuncAttributeMaxDynamicSharedMemorySize, FLUX_MX_SMEM);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[1][2], kb_flux_mx, FLUX_MX_TILE, FLUX_MX_SMEM);
     for (int m = 0; m < 2; m++)
         for (int p = 0; p < 3; p++) b->bsweep[m][p] = std::max(1, nb[m][p]) * b->sms;
     b->blocks_cells = b->sms * 8;

@@ -222,27 +222,61 @@ static __device__ __forceinline__ void compat_mixed(const ff Ql[5], const ff Qr[
 // ---------------------------------------------------------------------------
 // Gauss-point flux, mixed precision
 // ---------------------------------------------------------------------------
-static __device__ __noinline__ void gks_point_flux_mixed(const ff Ql[5], const ff Qr[5], const float dl[3][5],
-                                                         const float dr[3][5], const float d0[3][5],
-                                                         const MxGas G, float dtf, ff Fn[5], float dFn[5])
+// Inputs of one Gauss point, kept by the flux pass in shared memory as one
+// column per thread (slot-major, so a warp's accesses fall in distinct banks):
+//   values of Ql (0..4), Qr (5..9) as hi/lo pairs   GP_VAL(n, k, part)
+//   WENO slopes along the normal                     GP_SN(n, k)   k = 0..14 (l, r, 0)
+//   derivatives along the first tangential dir.      GP_S1(n, k)
+//   derivatives along the second tangential dir.     GP_S2(n, k)
+// for the two Gauss points n of one Gauss line; all slopes in index units.
+#define GP_VAL(n, k, part) (((n) * 10 + (k)) * 2 + (part))
+#define GP_SN(n, k) (40 + (n) * 15 + (k))
+#define GP_S1(n, k) (70 + (n) * 15 + (k))
+#define GP_S2(n, k) (100 + (n) * 15 + (k))
+constexpr int GP_SLOTS = 130;
+constexpr int FLUX_MX_BLOCK = 128;
+constexpr int FLUX_MX_SMEM = GP_SLOTS * FLUX_MX_BLOCK * (int)sizeof(float);
+
+// the slopes of one state (which = 0: Ql, 1: Qr, 2: Q0) in physical units
+static __device__ __forceinline__ void gp_slopes(const float *col, int st, int n, int which, float ihn, float ih1,
+                                                 float ih2, float dq[3][5])
+{
+#pragma unroll
+    for (int c = 0; c < 5; c++) {
+        dq[0][c] = col[GP_SN(n, which * 5 + c) * st] * ihn;
+        dq[1][c] = col[GP_S1(n, which * 5 + c) * st] * ih1;
+        dq[2][c] = col[GP_S2(n, which * 5 + c) * st] * ih2;
+    }
+}
+
+static __device__ __noinline__ void gks_point_flux_mixed(const float *col, int st, int n, float ihn, float ih1,
+                                                         float ih2, const MxGas G, float dtf, ff Fn[5], float dFn[5])
 {
     const float gm1 = G.gm1, K = G.K;
+    ff Ql[5], Qr[5];
+#pragma unroll
+    for (int c = 0; c < 5; c++) {
+        Ql[c] = ff{ col[GP_VAL(n, c, 0) * st], col[GP_VAL(n, c, 1) * st] };
+        Qr[c] = ff{ col[GP_VAL(n, 5 + c, 0) * st], col[GP_VAL(n, 5 + c, 1) * st] };
+    }
     ff Qm[5];
     float jq[5];
     const bool small_jump = compat_prepare(Ql, Qr, Qm, jq);
     // half-range terms of the two sides (FP32), one side at a time
     float b4l[5], w5l[5], b5l[5], w6l[5], b6l[5], b4r[5], w5r[5], b5r[5], w6r[5], b6r[5], cl[5], cr[5];
     {
-        float q[5];
+        float q[5], dq[3][5];
 #pragma unroll
         for (int c = 0; c < 5; c++) q[c] = ff_to_float(Ql[c]);
-        side_terms_mx<true>(q, dl, jq, small_jump, gm1, K, b4l, w5l, b5l, w6l, b6l, cl);
+        gp_slopes(col, st, n, 0, ihn, ih1, ih2, dq);
+        side_terms_mx<true>(q, dq, jq, small_jump, gm1, K, b4l, w5l, b5l, w6l, b6l, cl);
     }
     {
-        float q[5];
+        float q[5], dq[3][5];
 #pragma unroll
         for (int c = 0; c < 5; c++) q[c] = ff_to_float(Qr[c]);
-        side_terms_mx<false>(q, dr, jq, small_jump, gm1, K, b4r, w5r, b5r, w6r, b6r, cr);
+        gp_slopes(col, st, n, 1, ihn, ih1, ih2, dq);
+        side_terms_mx<false>(q, dq, jq, small_jump, gm1, K, b4r, w5r, b5r, w6r, b6r, cr);
     }
 
     // equilibrium state and its Euler flux in float-float
@@ -271,7 +305,8 @@ static __device__ __noinline__ void gks_point_flux_mixed(const ff Ql[5], const f
     const float tau = viscosity_f(G, T0) / p0f;
     float B2[5], B3[5], R0[5], B4m1[5], W5[5], B5[5], W6[5], B6[5];
     {
-        float s[5];
+        float s[5], d0[3][5];
+        gp_slopes(col, st, n, 2, ihn, ih1, ih2, d0);
         euler_dflux<0>(g0, d0[0], gm1, R0);
         euler_dflux<1>(g0, d0[1], gm1, s);
 #pragma unroll
@@ -467,8 +502,9 @@ static __device__ __forceinline__ float inv_metric_f(const Params &P, int e, con
     return e == 1 && P.stretched ? 1.0f / (float)tab[idx] : P.f_ih[e];
 }
 
+// sm: the block's dynamic shared memory, GP_SLOTS floats per thread
 static __device__ __forceinline__ void pos_flux_mx(const Params &P, int d, const Box &Bf, const Box &Bt, T1Mx in,
-                                                   double *__restrict__ F, double dt, long long t)
+                                                   double *__restrict__ F, double dt, long long t, float *sm)
 {
     const long long nf = box_count(Bf), nt = box_count(Bt);
     int p[3];
@@ -479,6 +515,8 @@ static __device__ __forceinline__ void pos_flux_mx(const Params &P, int d, const
     const float ihn = inv_metric_f(P, d, P.my_face, f);
     const float dtf = (float)dt;
     const MxGas G = mx_gas(P);
+    const int st = blockDim.x;
+    float *col = sm + threadIdx.x;
 
     ff Fs[5];
     float dFs[5];
@@ -490,8 +528,6 @@ static __device__ __forceinline__ void pos_flux_mx(const Params &P, int d, const
 #pragma unroll 1
     for (int m = 0; m < 2; m++) {
         const float ih1 = inv_metric_f(P, e1, P.my_gp, 2 * a + m);
-        ff gq[2][10];
-        float gs[2][15], gd1[2][15], gd2[2][15];
         // values Ql, Qr at the two Gauss points of this line
 #pragma unroll 1
         for (int k = 0; k < 10; k++) {
@@ -508,8 +544,11 @@ static __device__ __forceinline__ void pos_flux_mx(const Params &P, int d, const
             weno_prep(x, W);
             float vm, vp;
             weno_gauss_pair(W, vm, vp);
-            gq[0][k] = ff_add_f(ff{ H[2], L[2] }, vm);
-            gq[1][k] = ff_add_f(ff{ H[2], L[2] }, vp);
+            const ff g0 = ff_add_f(ff{ H[2], L[2] }, vm), g1 = ff_add_f(ff{ H[2], L[2] }, vp);
+            col[GP_VAL(0, k, 0) * st] = g0.hi;
+            col[GP_VAL(0, k, 1) * st] = g0.lo;
+            col[GP_VAL(1, k, 0) * st] = g1.hi;
+            col[GP_VAL(1, k, 1) * st] = g1.lo;
         }
         // derivatives along the second tangential direction of the quartic values
 #pragma unroll 1
@@ -523,7 +562,10 @@ static __device__ __forceinline__ void pos_flux_mx(const Params &P, int d, const
             }
 #pragma unroll
             for (int j = 0; j < 5; j++) x[j] = ff_dev(H[j], L[j], H[2], L[2]);
-            quartic_deriv_pair(x, gd2[0][k], gd2[1][k]);
+            float dm, dp;
+            quartic_deriv_pair(x, dm, dp);
+            col[GP_S2(0, k) * st] = dm;
+            col[GP_S2(1, k) * st] = dp;
         }
         // normal slopes (WENO) and first-direction derivatives (quartic value)
 #pragma unroll 1
@@ -538,28 +580,20 @@ static __device__ __forceinline__ void pos_flux_mx(const Params &P, int d, const
             }
             WenoPrep<float> W;
             weno_prep(x, W);
-            weno_gauss_pair(W, gs[0][k], gs[1][k]);
-            quartic_value_pair(y, gd1[0][k], gd1[1][k]);
+            float s0, s1, q0, q1;
+            weno_gauss_pair(W, s0, s1);
+            quartic_value_pair(y, q0, q1);
+            col[GP_SN(0, k) * st] = s0;
+            col[GP_SN(1, k) * st] = s1;
+            col[GP_S1(0, k) * st] = q0;
+            col[GP_S1(1, k) * st] = q1;
         }
 #pragma unroll 1
         for (int n = 0; n < 2; n++) {
             const float ih2 = inv_metric_f(P, e2, P.my_gp, 2 * b + n);
-            float dl[3][5], dr[3][5], d0[3][5];
-#pragma unroll
-            for (int c = 0; c < 5; c++) {
-                dl[0][c] = gs[n][c] * ihn;
-                dr[0][c] = gs[n][5 + c] * ihn;
-                d0[0][c] = gs[n][10 + c] * ihn;
-                dl[1][c] = gd1[n][c] * ih1;
-                dr[1][c] = gd1[n][5 + c] * ih1;
-                d0[1][c] = gd1[n][10 + c] * ih1;
-                dl[2][c] = gd2[n][c] * ih2;
-                dr[2][c] = gd2[n][5 + c] * ih2;
-                d0[2][c] = gd2[n][10 + c] * ih2;
-            }
             ff Fn[5];
             float dFn[5];
-            gks_point_flux_mixed(&gq[n][0], &gq[n][5], dl, dr, d0, G, dtf, Fn, dFn);
+            gks_point_flux_mixed(col, st, n, ihn, ih1, ih2, G, dtf, Fn, dFn);
 #pragma unroll
             for (int c = 0; c < 5; c++) {
                 Fs[c] = ff_add(Fs[c], ff_scale(Fn[c], 0.25f));  // Gauss weights 1/4 (exact)
