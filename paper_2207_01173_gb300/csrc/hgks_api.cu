@@ -230,6 +230,7 @@ extern "C" hgks_status hgks_create(const hgks_grid *grid, double gamma, double P
     if (!st) st = alloc(&h->fq, s.fq);
     if (!st) st = alloc(&h->t1, s.t1);
     if (!st && precision == HGKS_MIXED) st = alloc(&h->qf, s.pad);
+    if (!st) st = cuda_check(h, fp64_setup(), "flux kernel set-up");
     if (!st && precision == HGKS_MIXED) st = cuda_check(h, mixed_setup(), "mixed-precision kernel set-up");
     for (int d = 0; d < 3 && !st; d++) st = alloc(&h->F[d], s.F[d]);
     if (!st) st = alloc(&h->io[0], s.cells);

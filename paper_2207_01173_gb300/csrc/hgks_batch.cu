@@ -173,9 +173,10 @@ __global__ void __launch_bounds__(FLUX_MX_TILE, 3) kb_flux_mx(const Inst *__rest
     pos_flux_mx(in.P, d, Bf, Bt, t1_mx(in.t1, box_count(Bt)), in.F[d], in.ctl->dt, tl.start + threadIdx.x, gp_sm);
 }
 
-__global__ void __launch_bounds__(128) kb_flux(const Inst *__restrict__ I, const Tile *__restrict__ T, int ntiles,
-                                               int d)
+__global__ void __launch_bounds__(FLUX_BLOCK, 2) kb_flux(const Inst *__restrict__ I, const Tile *__restrict__ T,
+                                                         int ntiles, int d)
 {
+    extern __shared__ double flux_sm[];
     for (int k = blockIdx.x; k < ntiles; k += gridDim.x) {
         const Tile tl = T[k];
         const Inst &in = I[tl.inst];
@@ -183,7 +184,7 @@ __global__ void __launch_bounds__(128) kb_flux(const Inst *__restrict__ I, const
         const Box Bf = box_face(in.P, d), Bt = box_t1(in.P, d);
         const double dt = in.ctl->dt;
         for (long long t = tl.start + threadIdx.x; t < tl.start + tl.count; t += blockDim.x)
-            pos_flux(in.P, d, Bf, Bt, in.t1, in.F[d], dt, t);
+            pos_flux(in.P, d, Bf, Bt, in.t1, in.F[d], dt, t, flux_sm);
     }
 }
 
@@ -358,7 +359,8 @@ static void enqueue_batch_step(hgks_batch_t b, double cfl)
                     kb_normal<false><<<pgrid(b->cnt[wn], b->bsweep[0][0]), 128, 0, st>>>(I, T(wn), b->cnt[wn], d,
                                                                                         stage);
                     kb_tan1<false><<<pgrid(b->cnt[wt], b->bsweep[0][1]), 128, 0, st>>>(I, T(wt), b->cnt[wt], d);
-                    kb_flux<<<pgrid(b->cnt[wf], b->bsweep[0][2]), 128, 0, st>>>(I, T(wf), b->cnt[wf], d);
+                    kb_flux<<<pgrid(b->cnt[wf], b->bsweep[0][2]), FLUX_BLOCK, FLUX_SMEM, st>>>(I, T(wf), b->cnt[wf],
+                                                                                              d);
                 }
             }
             if (d == 1 && stage == 0 && b->any_walls) kb_wall<<<n, 256, 0, st>>>(I, n);
@@ -434,7 +436,8 @@ extern "C" hgks_status hgks_batch_create(hgks_t *handles, int n, hgks_batch_t *o
     int nb[2][3] = {};
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[0][0], kb_normal<false>, 128, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[0][1], kb_tan1<false>, 128, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[0][2], kb_flux, 128, 0);
+    cudaFuncSetAttribute((const void *)kb_flux, cudaFuncAttributeMaxDynamicSharedMemorySize, FLUX_SMEM);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[0][2], kb_flux, FLUX_BLOCK, FLUX_SMEM);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[1][0], kb_normal<true>, 128, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[1][1], kb_tan1<true>, 128, 0);
     cudaFuncSetAttribute((const void *)kb_flux_mx, cudaFuncAttributeMaxDynamicSharedMemorySize, FLUX_MX_SMEM);

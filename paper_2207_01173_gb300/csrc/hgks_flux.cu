@@ -33,12 +33,23 @@ __global__ void __launch_bounds__(128) k_tan1(Params P, int d, Box Bt, Box Bq, c
     pos_tan1(P, d, Bt, Bq, fq, t1, t);
 }
 
-__global__ void __launch_bounds__(128) k_flux(Params P, int d, Box Bf, Box Bt, const double *__restrict__ t1,
-                                              double *__restrict__ F, const Ctl *__restrict__ ctl)
+// two blocks of 128 per SM: 255 registers and FLUX_SMEM (113.7 kB) of staged
+// Gauss-point inputs each
+__global__ void __launch_bounds__(FLUX_BLOCK, 2) k_flux(Params P, int d, Box Bf, Box Bt,
+                                                        const double *__restrict__ t1, double *__restrict__ F,
+                                                        const Ctl *__restrict__ ctl)
 {
+    extern __shared__ double flux_sm[];
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= box_count(Bf) || ctl->flag) return;
-    pos_flux(P, d, Bf, Bt, t1, F, ctl->dt, t);
+    pos_flux(P, d, Bf, Bt, t1, F, ctl->dt, t, flux_sm);
+}
+
+// opt in to the dynamic shared memory of the FP64 flux kernel on the current
+// device; called when a handle is created, before any launch or capture
+cudaError_t fp64_setup()
+{
+    return cudaFuncSetAttribute((const void *)k_flux, cudaFuncAttributeMaxDynamicSharedMemorySize, FLUX_SMEM);
 }
 
 static inline unsigned grid_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
@@ -56,7 +67,7 @@ void launch_tan1(const Params &P, int d, const double *fq, double *t1, const Ctl
 void launch_flux(const Params &P, int d, const double *t1, double *F, const Ctl *ctl, cudaStream_t st)
 {
     Box Bf = box_face(P, d), Bt = box_t1(P, d);
-    k_flux<<<grid_for(box_count(Bf), 128), 128, 0, st>>>(P, d, Bf, Bt, t1, F, ctl);
+    k_flux<<<grid_for(box_count(Bf), FLUX_BLOCK), FLUX_BLOCK, FLUX_SMEM, st>>>(P, d, Bf, Bt, t1, F, ctl);
 }
 
 }  // namespace hgks

@@ -63,6 +63,7 @@ void launch_flux(const Params &P, int d, const double *t1, double *F, const Ctl 
 void launch_wall(const Params &P, const double *Fy, Ctl *ctl, double lxlz, cudaStream_t st);
 // mixed-precision sweep passes (which: 0 normal, 1 first tangential, 2 flux),
 // using the same fq / t1 buffers as the FP64 passes
+cudaError_t fp64_setup();
 cudaError_t mixed_setup();
 void launch_split_mixed(const Params &P, const double *q, double *qf, const Ctl *ctl, cudaStream_t st);
 void launch_sweep_mixed(const Params &P, int d, const double *qf, double *fq, double *t1, double *F, const Ctl *ctl,

@@ -249,7 +249,7 @@ static __device__ __forceinline__ void gp_slopes(const float *col, int st, int n
     }
 }
 
-static __device__ __noinline__ void gks_point_flux_mixed(const float *col, int st, int n, float ihn, float ih1,
+static __device__ __forceinline__ void gks_point_flux_mixed(const float *col, int st, int n, float ihn, float ih1,
                                                          float ih2, const MxGas G, float dtf, ff Fn[5], float dFn[5])
 {
     const float gm1 = G.gm1, K = G.K;
