@@ -256,17 +256,19 @@ static __device__ __forceinline__ void cell_rhs(const Params &P, const double *q
     const long long l0 = ((long long)k * ny + j) * (nx + 1) + i;
     const long long l1 = ((long long)k * (ny + 1) + j) * nx + i;
     const long long l2 = ((long long)k * ny + j) * nx + i;
-    const double vol = P.h[0] * P.hy_cell[j] * P.h[2];
+    // one reciprocal of the cell volume instead of ten FP64 divisions (the
+    // update is FP64-bound; the results differ from division by <= 1 ulp)
+    const double ivol = 1.0 / (P.h[0] * P.hy_cell[j] * P.h[2]);
 #pragma unroll
     for (int c = 0; c < 5; c++) {
         double sx = F[0][c * n0 + l0 + 1] - F[0][c * n0 + l0];
         double sy = F[1][c * n1 + l1 + nx] - F[1][c * n1 + l1];
         double sz = F[2][c * n2 + l2 + (long long)nx * ny] - F[2][c * n2 + l2];
-        L[c] = -((sx + sy) + sz) / vol;
+        L[c] = -((sx + sy) + sz) * ivol;
         double tx = F[0][(5 + c) * n0 + l0 + 1] - F[0][(5 + c) * n0 + l0];
         double ty = F[1][(5 + c) * n1 + l1 + nx] - F[1][(5 + c) * n1 + l1];
         double tz = F[2][(5 + c) * n2 + l2 + (long long)nx * ny] - F[2][(5 + c) * n2 + l2];
-        dL[c] = -((tx + ty) + tz) / vol;
+        dL[c] = -((tx + ty) + tz) * ivol;
     }
     if (P.has_force) {
         // source (0, rho G, rho u.G) and its time derivative (0, G L_rho, G.L_mom)
@@ -304,13 +306,15 @@ static __device__ __forceinline__ bool pos_update(const Params &P, int stage, co
     double L[5], dL[5], A[5];
     cell_rhs(P, q, F, i, j, k, p, L, dL);
     bool ok = true;
+    const double dt2 = dt * dt;
     if (stage == 1) {
         double B[5];
+        const double h1 = 0.5 * dt, h2 = 0.125 * dt2, s2 = dt2 * (1.0 / 6.0);
 #pragma unroll
         for (int c = 0; c < 5; c++) {
             double Q = q[c * P.cs + p];
-            A[c] = Q + 0.5 * dt * L[c] + 0.125 * dt * dt * dL[c];
-            B[c] = Q + dt * L[c] + (dt * dt / 6.0) * dL[c];
+            A[c] = Q + h1 * L[c] + h2 * dL[c];
+            B[c] = Q + dt * L[c] + s2 * dL[c];
             oa[c * P.cs + p] = A[c];
             ob[c * P.cs + p] = B[c];
         }
@@ -319,7 +323,7 @@ static __device__ __forceinline__ bool pos_update(const Params &P, int stage, co
         // oa = r + dt^2/3 dL(Q*), r = the stage-1 accumulator passed as ob
 #pragma unroll
         for (int c = 0; c < 5; c++) {
-            A[c] = ob[c * P.cs + p] + (dt * dt / 3.0) * dL[c];
+            A[c] = ob[c * P.cs + p] + (dt2 * (1.0 / 3.0)) * dL[c];
             oa[c * P.cs + p] = A[c];
         }
         ok = state_ok(A);

@@ -529,7 +529,7 @@ static __device__ __forceinline__ void pos_flux_mx(const Params &P, int d, const
     for (int m = 0; m < 2; m++) {
         const float ih1 = inv_metric_f(P, e1, P.my_gp, 2 * a + m);
         // values Ql, Qr at the two Gauss points of this line
-#pragma unroll 1
+#pragma unroll 2  // two rows of loads in flight
         for (int k = 0; k < 10; k++) {
             const long long off = (long long)(m * 25 + k) * nt + base;
             float H[5], L[5], x[5];
@@ -551,7 +551,7 @@ static __device__ __forceinline__ void pos_flux_mx(const Params &P, int d, const
             col[GP_VAL(1, k, 1) * st] = g1.lo;
         }
         // derivatives along the second tangential direction of the quartic values
-#pragma unroll 1
+#pragma unroll 2
         for (int k = 0; k < 15; k++) {
             const long long off = (long long)(m * 25 + 10 + k) * nt + base;
             float H[5], L[5], x[5];
@@ -568,7 +568,7 @@ static __device__ __forceinline__ void pos_flux_mx(const Params &P, int d, const
             col[GP_S2(1, k) * st] = dp;
         }
         // normal slopes (WENO) and first-direction derivatives (quartic value)
-#pragma unroll 1
+#pragma unroll 2
         for (int k = 0; k < 15; k++) {
             const float *ss = in.ts + (long long)(m * 30 + k) * nt + base;
             const float *sd = in.ts + (long long)(m * 30 + 15 + k) * nt + base;
