@@ -229,7 +229,7 @@ def serve_leg(hg, args, capacity):
     free, _ = torch.cuda.mem_get_info()
     budget = int(min(0.8 * free, args.serve_budget_gb * 2 ** 30))
     eng = CudaEngine(precision=hg.MIXED, cfl=CFL)
-    srv = Server(eng, budget, max_chunk=args.serve_chunk)
+    srv = Server(eng, budget, max_chunk=args.serve_chunk, policy=args.serve_policy, age_s=args.serve_age)
     with ClockSampler(torch.cuda.current_device()) as clk:
         res, summ = srv.run(reqs)
     eng.close()
@@ -237,7 +237,9 @@ def serve_leg(hg, args, capacity):
                          "N in {64,96,128}) solves of 20-200 steps, mixed precision; first %d of 500 requests"
                 % len(reqs),
                 arrival_rate_per_s=rate, capacity_cell_updates_per_s=capacity, mean_work_cell_updates=mean_work,
-                max_chunk=args.serve_chunk, batch_rebuilds=eng.rebuilds, clocks=clk.summary(),
+                max_chunk=args.serve_chunk, policy=args.serve_policy, age_s=args.serve_age,
+                batch_rebuilds=eng.rebuilds,
+                clocks=clk.summary(),
                 latency_percentiles="numpy linear interpolation over completed requests")
     return summ
 
@@ -344,7 +346,7 @@ def run_ours(args, rank, world, local_rank):
     batched = None if args.no_batched else batched_leg(hg, args, stream)
     serve = None
     if rank == 0 and args.serve_requests > 0:
-        cap = batched["mixed"]["value"] if batched else (mixed["value"] if mixed else value)
+        cap = args.serve_capacity or (batched["mixed"]["value"] if batched else (mixed["value"] if mixed else value))
         serve = serve_leg(hg, args, cap)
 
     if rank != 0:
@@ -406,6 +408,11 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=12)
     ap.add_argument("--serve-budget-gb", type=float, default=96.0)
     ap.add_argument("--serve-chunk", type=int, default=8)
+    ap.add_argument("--serve-policy", choices=["fair", "srpt"], default="srpt")
+    ap.add_argument("--serve-age", type=float, default=10.0,
+                    help="srpt aging: remaining work is divided by 1 + wait / this many seconds")
+    ap.add_argument("--serve-capacity", type=float, default=0.0,
+                    help="cell-updates/s that sets the arrival rate (default: the measured batched mixed rate)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")

@@ -93,14 +93,28 @@ class CudaEngine:
 
 
 class Server:
+    """policy "fair": every running request advances in every chunk.
+    policy "srpt": each chunk advances the running requests with the least
+    remaining work (cells x steps left), smallest first, until they hold at
+    least `fill_cells` cells; the others keep their memory and wait.  Small
+    requests then finish without waiting behind large ones, and the batch
+    still fills the GPU.  With age_s > 0 the remaining work of a request is
+    discounted by (1 + age / age_s), age the time since its arrival, so a
+    large request is not starved by a stream of small ones."""
+
     def __init__(self, engine, budget_bytes, max_chunk=8, keep_state=False, clock=time.perf_counter,
-                 sleep=time.sleep):
+                 sleep=time.sleep, policy="fair", fill_cells=8 * 2 ** 20, age_s=0.0):
+        if policy not in ("fair", "srpt"):
+            raise ValueError("policy must be 'fair' or 'srpt'")
         self.engine = engine
         self.budget = int(budget_bytes)
         self.max_chunk = int(max_chunk)
         self.keep_state = keep_state
         self.clock = clock
         self.sleep = sleep
+        self.policy = policy
+        self.fill_cells = int(fill_cells)
+        self.age_s = float(age_s)
         self._cancel = set()
 
     def cancel(self, rid):
@@ -171,7 +185,7 @@ class Server:
                 if pending:
                     self.sleep(max(0.0, pending[0]["t"] - (self.clock() - t0)))
                 continue
-            ids = sorted(running)
+            ids = self._working_set(running, now)
             chunk = min(self.max_chunk, min(running[i]["req"]["steps"] - running[i]["done"] for i in ids))
             c0 = self.clock()
             counts = self.engine.step([running[i]["h"] for i in ids], chunk)
@@ -188,6 +202,23 @@ class Server:
                 if c >= run["req"]["steps"]:
                     retire(i, "done", now)
         return results, summarize(results, peak, self.budget, conc, chunks)
+
+    def _working_set(self, running, now):
+        if self.policy == "fair":
+            return sorted(running)
+
+        def left(i):
+            r = running[i]
+            work = int(np.prod(r["req"]["n"])) * (r["req"]["steps"] - r["done"])
+            return work / (1.0 + max(0.0, now - r["req"]["t"]) / self.age_s) if self.age_s > 0 else work
+
+        ids, cells = [], 0
+        for i in sorted(running, key=lambda i: (left(i), i)):
+            if ids and cells >= self.fill_cells:
+                break
+            ids.append(i)
+            cells += int(np.prod(running[i]["req"]["n"]))
+        return sorted(ids)
 
 
 def summarize(results, peak_bytes, budget, conc, chunks):

@@ -137,3 +137,43 @@ def test_serve_stream_is_seeded_and_mixed():
     assert min(r["steps"] for r in a) >= 20 and max(r["steps"] for r in a) <= 200
     gaps = np.diff([0.0] + [r["arrival"] for r in a])
     assert (gaps > 0).all() and 0.85 < gaps.mean() < 1.15  # unit-rate Poisson arrivals
+
+
+def test_srpt_lets_small_requests_pass_large_ones():
+    # a large request runs; a small one arrives; under "srpt" with a fill
+    # target below the large request's size, the small one runs alone first
+    reqs = [req(0, 0.0, 60, 100), req(1, 1.0, 10, 10)]
+    out = {}
+    for policy in ("fair", "srpt"):
+        clk = FakeClock()
+        eng = FakeEngine(clk)
+        srv = Server(eng, 10 ** 9, max_chunk=8, clock=clk, sleep=clk.sleep, policy=policy, fill_cells=1)
+        res, summ = srv.run(reqs)
+        assert summ["done"] == 2 and res[0]["steps_done"] == 100 and res[1]["steps_done"] == 10
+        out[policy] = (res, eng)
+    fair, srpt = out["fair"][0], out["srpt"][0]
+    assert srpt[1]["latency"] < fair[1]["latency"]
+    assert srpt[1]["t_done"] < srpt[0]["t_done"]
+    # while the small request ran, the large one waited (working set of one)
+    assert any(h == (1,) for h, _ in out["srpt"][1].steps_log)
+    with pytest.raises(ValueError):
+        Server(FakeEngine(FakeClock()), 1, policy="lifo")
+
+
+def test_srpt_aging_lets_a_long_waiting_request_in():
+    # a medium request waits behind a sustained stream of small ones (each
+    # arrives a little before the previous one is done); with pure SRPT it
+    # runs only after the stream, with aging it gets in once the ratio of its
+    # age to theirs outweighs its 4.7x larger remaining work
+    reqs = [req(0, 0.0, 12, 20), req(1, 0.001, 16, 40)] + [req(i, 0.03 * (i - 1), 12, 20) for i in range(2, 70)]
+    done = {}
+    for age in (0.0, 0.05):
+        clk = FakeClock()
+        srv = Server(FakeEngine(clk), 10 ** 9, max_chunk=4, clock=clk, sleep=clk.sleep, policy="srpt",
+                     fill_cells=1, age_s=age)
+        res, summ = srv.run(reqs)
+        assert summ["done"] == 70
+        last_small = max(r["t_done"] for i, r in res.items() if i != 1)
+        done[age] = (res[1]["t_done"], last_small)
+    assert done[0.0][0] > done[0.0][1]    # pure SRPT: after the whole stream
+    assert done[0.05][0] < done[0.05][1]  # aging: before the stream ends
