@@ -154,23 +154,22 @@ __global__ void __launch_bounds__(128, MX ? 4 : 1) kb_tan1(const Inst *__restric
 }
 
 // The mixed flux pass is the one pass that is not persistent: it launches one
-// block per tile of exactly FLUX_MX_TILE positions (one per thread), and the
-// hardware block scheduler hands out the tiles.  A persistent loop keeps its
-// state live across the flux, which at the 128-register budget of this
-// latency-bound kernel raised the spills from 48 to 232 bytes and cost 40 %.
-constexpr int FLUX_MX_TILE = FLUX_MX_BLOCK;
-
-__global__ void __launch_bounds__(FLUX_MX_TILE, 3) kb_flux_mx(const Inst *__restrict__ I,
-                                                              const Tile *__restrict__ T, int ntiles, int d)
+// block per flux tile of 32 x 4 faces (flux_mx_tile; a work-list entry per
+// tile), and the hardware block scheduler hands out the tiles.  A persistent
+// loop keeps its state live across the flux, which at the register budget of
+// this latency-bound kernel raised the spills from 48 to 232 bytes and cost
+// 40 %.
+__global__ void __launch_bounds__(FLUX_MX_BLOCK, 3) kb_flux_mx(const Inst *__restrict__ I,
+                                                               const Tile *__restrict__ T, int ntiles, int d)
 {
     extern __shared__ float gp_sm[];
     const int k = blockIdx.x;
     if (k >= ntiles) return;
     const Tile tl = T[k];
     const Inst &in = I[tl.inst];
-    if (in.ctl->flag || (long long)threadIdx.x >= tl.count) return;
+    if (in.ctl->flag) return;
     const Box Bf = box_face(in.P, d), Bt = box_t1(in.P, d);
-    pos_flux_mx(in.P, d, Bf, Bt, t1_mx(in.t1, box_count(Bt)), in.F[d], in.ctl->dt, tl.start + threadIdx.x, gp_sm);
+    flux_mx_tile(in.P, d, Bf, Bt, t1_mx(in.t1, box_count(Bt)), in.F[d], in.ctl->dt, tl.start, gp_sm);
 }
 
 __global__ void __launch_bounds__(FLUX_BLOCK, 2) kb_flux(const Inst *__restrict__ I, const Tile *__restrict__ T,
@@ -312,7 +311,8 @@ static hgks_status build_tiles(hgks_batch_t b)
                 const int mixed = (w - WL_SWEEP) / 9, pass = (w - WL_SWEEP) / 3 % 3, d = (w - WL_SWEEP) % 3;
                 if (mixed != b->inst[i].mixed) continue;
                 const Box B = pass == 0 ? box_fq(P, d) : pass == 1 ? box_t1(P, d) : box_face(P, d);
-                add(w, i, box_count(B), (mixed && pass == 2) ? FLUX_MX_TILE : b->tile_sweep);
+                if (mixed && pass == 2) add(w, i, flux_tiling(P, d).count, 1);  // one entry per flux tile
+                else add(w, i, box_count(B), b->tile_sweep);
             }
         }
         b->cnt[w] = (int)all.size() - b->off[w];
@@ -354,7 +354,8 @@ static void enqueue_batch_step(hgks_batch_t b, double cfl)
                     kb_normal<true><<<pgrid(b->cnt[wn], b->bsweep[1][0]), 128, 0, st>>>(I, T(wn), b->cnt[wn], d,
                                                                                        stage);
                     kb_tan1<true><<<pgrid(b->cnt[wt], b->bsweep[1][1]), 128, 0, st>>>(I, T(wt), b->cnt[wt], d);
-                    kb_flux_mx<<<(unsigned)b->cnt[wf], FLUX_MX_TILE, FLUX_MX_SMEM, st>>>(I, T(wf), b->cnt[wf], d);
+                    kb_flux_mx<<<(unsigned)b->cnt[wf], FLUX_MX_BLOCK, FLUX_MX_TILE_SMEM, st>>>(I, T(wf), b->cnt[wf],
+                                                                                              d);
                 } else {
                     kb_normal<false><<<pgrid(b->cnt[wn], b->bsweep[0][0]), 128, 0, st>>>(I, T(wn), b->cnt[wn], d,
                                                                                         stage);
@@ -440,8 +441,8 @@ extern "C" hgks_status hgks_batch_create(hgks_t *handles, int n, hgks_batch_t *o
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[0][2], kb_flux, FLUX_BLOCK, FLUX_SMEM);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[1][0], kb_normal<true>, 128, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[1][1], kb_tan1<true>, 128, 0);
-    cudaFuncSetAttribute((const void *)kb_flux_mx, cudaFuncAttributeMaxDynamicSharedMemorySize, FLUX_MX_SMEM);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[1][2], kb_flux_mx, FLUX_MX_TILE, FLUX_MX_SMEM);
+    cudaFuncSetAttribute((const void *)kb_flux_mx, cudaFuncAttributeMaxDynamicSharedMemorySize, FLUX_MX_TILE_SMEM);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[1][2], kb_flux_mx, FLUX_MX_BLOCK, FLUX_MX_TILE_SMEM);
     for (int m = 0; m < 2; m++)
         for (int p = 0; p < 3; p++) b->bsweep[m][p] = std::max(1, nb[m][p]) * b->sms;
     b->blocks_cells = b->sms * 8;

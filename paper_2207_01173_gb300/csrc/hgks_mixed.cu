@@ -28,23 +28,24 @@ __global__ void __launch_bounds__(128, 4) k_tan1_mx(Params P, int d, Box Bt, Box
     pos_tan1_mx(P, d, Bt, Bq, in, o, t);
 }
 
-// The Gauss-point inputs live in dynamic shared memory (GP_SLOTS floats per
-// thread, 66.5 kB per block of 128), which allows three blocks per SM; the
-// register budget follows (170 per thread).
+// One block per tile of 32 x 4 faces (flux_mx_tile); dynamic shared memory
+// holds the Gauss-point inputs (GP_SLOTS floats per thread, 66.5 kB) and the
+// staged t1 rows (4 kB), which allows three blocks per SM and so 170
+// registers per thread.
 __global__ void __launch_bounds__(FLUX_MX_BLOCK, 3) k_flux_mx(Params P, int d, Box Bf, Box Bt, T1Mx in,
                                                               double *__restrict__ F, const Ctl *__restrict__ ctl)
 {
     extern __shared__ float gp_sm[];
-    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= box_count(Bf) || ctl->flag) return;
-    pos_flux_mx(P, d, Bf, Bt, in, F, ctl->dt, t, gp_sm);
+    if (ctl->flag) return;
+    flux_mx_tile(P, d, Bf, Bt, in, F, ctl->dt, blockIdx.x, gp_sm);
 }
 
 // opt in to the dynamic shared memory of the mixed flux kernel on the current
 // device; called when a mixed handle is created, before any launch or capture
 cudaError_t mixed_setup()
 {
-    return cudaFuncSetAttribute((const void *)k_flux_mx, cudaFuncAttributeMaxDynamicSharedMemorySize, FLUX_MX_SMEM);
+    return cudaFuncSetAttribute((const void *)k_flux_mx, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                FLUX_MX_TILE_SMEM);
 }
 
 static inline unsigned gridx(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
@@ -66,8 +67,8 @@ void launch_sweep_mixed(const Params &P, int d, const double *qf, double *fq, do
     if (which == 0) k_normal_mx<<<gridx(nq, 128), 128, 0, st>>>(P, d, Bq, qh, qh + 5 * P.cs, fq_mx(fq, nq), ctl);
     else if (which == 1) k_tan1_mx<<<gridx(nt, 128), 128, 0, st>>>(P, d, Bt, Bq, fq_mx(fq, nq), t1_mx(t1, nt), ctl);
     else
-        k_flux_mx<<<gridx(box_count(Bf), FLUX_MX_BLOCK), FLUX_MX_BLOCK, FLUX_MX_SMEM, st>>>(P, d, Bf, Bt,
-                                                                                          t1_mx(t1, nt), F, ctl);
+        k_flux_mx<<<(unsigned)flux_tiling(P, d).count, FLUX_MX_BLOCK, FLUX_MX_TILE_SMEM, st>>>(P, d, Bf, Bt,
+                                                                                             t1_mx(t1, nt), F, ctl);
 }
 
 }  // namespace hgks

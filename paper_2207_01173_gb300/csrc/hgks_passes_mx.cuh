@@ -502,22 +502,103 @@ static __device__ __forceinline__ float inv_metric_f(const Params &P, int e, con
     return e == 1 && P.stretched ? 1.0f / (float)tab[idx] : P.f_ih[e];
 }
 
-// sm: the block's dynamic shared memory, GP_SLOTS floats per thread
-static __device__ __forceinline__ void pos_flux_mx(const Params &P, int d, const Box &Bf, const Box &Bt, T1Mx in,
-                                                   double *__restrict__ F, double dt, long long t, float *sm)
+// ---------------------------------------------------------------------------
+// pass 3 on block tiles: 32 faces along x by 4 along the second tangential
+// direction e2 (one warp per e2 row).  The four e2 rows of a tile share the
+// eight t1 rows b0-2 .. b0+5 of every row type, so the block stages those in
+// shared memory once (8 instead of 20 row loads per 4 faces) and prefetches
+// the next row type with cp.async while it reduces the current one.
+// ---------------------------------------------------------------------------
+constexpr int FT_X = 32, FT_B = 4, FT_ROWS = FT_B + 4;
+constexpr int FT_STAGE = 2 * 2 * FT_ROWS * FT_X;  // floats: [buffer][array][row][x]
+constexpr int FLUX_MX_TILE_SMEM = FLUX_MX_SMEM + FT_STAGE * (int)sizeof(float);
+
+struct FluxTiling {
+    int e2, other, nxt, nbt, no;
+    long long count;
+};
+__host__ __device__ inline FluxTiling flux_tiling(const Params &P, int d)
 {
+    FluxTiling f;
+    f.e2 = tdir(d, 1);
+    f.other = d == 2 ? 2 : 1;  // the axis that is neither x nor e2
+    const int E0 = P.n[0] + (d == 0 ? 1 : 0);
+    f.nxt = (E0 + FT_X - 1) / FT_X;
+    f.nbt = (P.n[f.e2] + FT_B - 1) / FT_B;
+    f.no = P.n[f.other] + (f.other == d ? 1 : 0);
+    f.count = (long long)f.nxt * f.nbt * f.no;
+    return f;
+}
+
+static __device__ __forceinline__ void cp_async4(float *dst, const float *src)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(src) : "memory");
+}
+static __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+static __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// the two source arrays of row type it (0..79: line m = it / 40; 0..9 WENO
+// values, 10..24 quartic values, 25..39 slopes and first-direction derivatives)
+static __device__ __forceinline__ void ft_planes(const T1Mx &in, long long nt, int it, const float *&A,
+                                                 const float *&B)
+{
+    const int m = it / 40, k = it % 40;
+    if (k < 25) {
+        A = in.th + (long long)(m * 25 + k) * nt;
+        B = in.tl + (long long)(m * 25 + k) * nt;
+    } else {
+        A = in.ts + (long long)(m * 30 + (k - 25)) * nt;
+        B = in.ts + (long long)(m * 30 + 15 + (k - 25)) * nt;
+    }
+}
+
+// sm: GP_SLOTS floats per thread (Gauss-point inputs), then FT_STAGE floats
+static __device__ __forceinline__ void flux_mx_tile(const Params &P, int d, const Box &Bf, const Box &Bt, T1Mx in,
+                                                    double *__restrict__ F, double dt, long long T, float *sm)
+{
+    const FluxTiling ft = flux_tiling(P, d);
     const long long nf = box_count(Bf), nt = box_count(Bt);
+    const int xt = (int)(T % ft.nxt);
+    const long long r1 = T / ft.nxt;
+    const int bt = (int)(r1 % ft.nbt), o = (int)(r1 / ft.nbt);
+    const int x0 = xt * FT_X, b0 = bt * FT_B;
+    const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
+    const int e1 = tdir(d, 0), e2 = ft.e2;
+    // this thread's face
     int p[3];
-    bpos(Bf, t, p);
-    const int e1 = tdir(d, 0), e2 = tdir(d, 1);
-    const int f = p[d], a = p[e1], b = p[e2];
-    const long long base = blin(Bt, p), s2 = bstride(Bt, e2);
-    const float ihn = inv_metric_f(P, d, P.my_face, f);
+    p[0] = x0 + lane;
+    p[e2] = b0 + wb;
+    p[ft.other] = o;
+    const bool valid = p[0] < Bf.E[0] && p[e2] < Bf.E[e2];
+    // first t1 row of the tile (e2 index b0 - 2, x0) and the row stride
+    int q0[3] = { x0, 0, 0 };
+    q0[e2] = b0 - 2;
+    q0[ft.other] = o;
+    const long long base0 = blin(Bt, q0), s2 = bstride(Bt, e2);
+    const int xlim = Bf.E[0] - x0;            // lanes with x in range
+    const int rlim = P.n[e2] + 3 - b0;        // rows r with e2 index b0 - 2 + r <= n + 1
+    float *gp = sm, *stage = sm + GP_SLOTS * FLUX_MX_BLOCK;
+    const int st = blockDim.x;
+    float *col = gp + threadIdx.x;
+
+    auto issue = [&](int it) {
+        const float *A, *B;
+        ft_planes(in, nt, it, A, B);
+        float *buf = stage + (it & 1) * (2 * FT_ROWS * FT_X);
+#pragma unroll
+        for (int i = 0; i < (2 * FT_ROWS * FT_X) / FLUX_MX_BLOCK; i++) {
+            const int e = threadIdx.x + i * FLUX_MX_BLOCK;
+            const int seg = e >> 5, l = e & 31, arr = seg / FT_ROWS, r = seg % FT_ROWS;
+            if (l < xlim && r <= rlim) cp_async4(buf + e, (arr ? B : A) + base0 + r * s2 + l);
+        }
+        cp_async_commit();
+    };
+
+    const float ihn = valid ? inv_metric_f(P, d, P.my_face, p[d]) : 0.0f;
     const float dtf = (float)dt;
     const MxGas G = mx_gas(P);
-    const int st = blockDim.x;
-    float *col = sm + threadIdx.x;
-
     ff Fs[5];
     float dFs[5];
 #pragma unroll
@@ -525,86 +606,81 @@ static __device__ __forceinline__ void pos_flux_mx(const Params &P, int d, const
         Fs[c] = ff{ 0.0f, 0.0f };
         dFs[c] = 0.0f;
     }
+    issue(0);
 #pragma unroll 1
-    for (int m = 0; m < 2; m++) {
-        const float ih1 = inv_metric_f(P, e1, P.my_gp, 2 * a + m);
-        // values Ql, Qr at the two Gauss points of this line
-#pragma unroll 2  // two rows of loads in flight
-        for (int k = 0; k < 10; k++) {
-            const long long off = (long long)(m * 25 + k) * nt + base;
-            float H[5], L[5], x[5];
+    for (int it = 0; it < 80; it++) {
+        if (it + 1 < 80) {
+            issue(it + 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        const float *buf = stage + (it & 1) * (2 * FT_ROWS * FT_X);
+        const int k = it % 40;
+        if (valid) {
+            float X[5], Y[5];
 #pragma unroll
             for (int j = 0; j < 5; j++) {
-                H[j] = in.th[off + (j - 2) * s2];
-                L[j] = in.tl[off + (j - 2) * s2];
+                X[j] = buf[(0 * FT_ROWS + wb + j) * FT_X + lane];
+                Y[j] = buf[(1 * FT_ROWS + wb + j) * FT_X + lane];
             }
+            if (k < 25) {  // float-float values: deviations about the centre row
+                float x[5];
 #pragma unroll
-            for (int j = 0; j < 5; j++) x[j] = ff_dev(H[j], L[j], H[2], L[2]);
-            WenoPrep<float> W;
-            weno_prep(x, W);
-            float vm, vp;
-            weno_gauss_pair(W, vm, vp);
-            const ff g0 = ff_add_f(ff{ H[2], L[2] }, vm), g1 = ff_add_f(ff{ H[2], L[2] }, vp);
-            col[GP_VAL(0, k, 0) * st] = g0.hi;
-            col[GP_VAL(0, k, 1) * st] = g0.lo;
-            col[GP_VAL(1, k, 0) * st] = g1.hi;
-            col[GP_VAL(1, k, 1) * st] = g1.lo;
-        }
-        // derivatives along the second tangential direction of the quartic values
-#pragma unroll 2
-        for (int k = 0; k < 15; k++) {
-            const long long off = (long long)(m * 25 + 10 + k) * nt + base;
-            float H[5], L[5], x[5];
-#pragma unroll
-            for (int j = 0; j < 5; j++) {
-                H[j] = in.th[off + (j - 2) * s2];
-                L[j] = in.tl[off + (j - 2) * s2];
+                for (int j = 0; j < 5; j++) x[j] = ff_dev(X[j], Y[j], X[2], Y[2]);
+                if (k < 10) {
+                    WenoPrep<float> W;
+                    weno_prep(x, W);
+                    float vm, vp;
+                    weno_gauss_pair(W, vm, vp);
+                    const ff g0 = ff_add_f(ff{ X[2], Y[2] }, vm), g1 = ff_add_f(ff{ X[2], Y[2] }, vp);
+                    col[GP_VAL(0, k, 0) * st] = g0.hi;
+                    col[GP_VAL(0, k, 1) * st] = g0.lo;
+                    col[GP_VAL(1, k, 0) * st] = g1.hi;
+                    col[GP_VAL(1, k, 1) * st] = g1.lo;
+                } else {
+                    float dm, dp;
+                    quartic_deriv_pair(x, dm, dp);
+                    col[GP_S2(0, k - 10) * st] = dm;
+                    col[GP_S2(1, k - 10) * st] = dp;
+                }
+            } else {  // normal slopes (WENO) and first-direction derivatives (quartic value)
+                WenoPrep<float> W;
+                weno_prep(X, W);
+                float s0, s1, q0v, q1v;
+                weno_gauss_pair(W, s0, s1);
+                quartic_value_pair(Y, q0v, q1v);
+                col[GP_SN(0, k - 25) * st] = s0;
+                col[GP_SN(1, k - 25) * st] = s1;
+                col[GP_S1(0, k - 25) * st] = q0v;
+                col[GP_S1(1, k - 25) * st] = q1v;
             }
-#pragma unroll
-            for (int j = 0; j < 5; j++) x[j] = ff_dev(H[j], L[j], H[2], L[2]);
-            float dm, dp;
-            quartic_deriv_pair(x, dm, dp);
-            col[GP_S2(0, k) * st] = dm;
-            col[GP_S2(1, k) * st] = dp;
-        }
-        // normal slopes (WENO) and first-direction derivatives (quartic value)
-#pragma unroll 2
-        for (int k = 0; k < 15; k++) {
-            const float *ss = in.ts + (long long)(m * 30 + k) * nt + base;
-            const float *sd = in.ts + (long long)(m * 30 + 15 + k) * nt + base;
-            float x[5], y[5];
-#pragma unroll
-            for (int j = 0; j < 5; j++) {
-                x[j] = ss[(j - 2) * s2];
-                y[j] = sd[(j - 2) * s2];
-            }
-            WenoPrep<float> W;
-            weno_prep(x, W);
-            float s0, s1, q0, q1;
-            weno_gauss_pair(W, s0, s1);
-            quartic_value_pair(y, q0, q1);
-            col[GP_SN(0, k) * st] = s0;
-            col[GP_SN(1, k) * st] = s1;
-            col[GP_S1(0, k) * st] = q0;
-            col[GP_S1(1, k) * st] = q1;
-        }
+            if (k == 39) {  // all inputs of line m: the two Gauss-point fluxes
+                const int m = it / 40;
+                const float ih1 = inv_metric_f(P, e1, P.my_gp, 2 * p[e1] + m);
 #pragma unroll 1
-        for (int n = 0; n < 2; n++) {
-            const float ih2 = inv_metric_f(P, e2, P.my_gp, 2 * b + n);
-            ff Fn[5];
-            float dFn[5];
-            gks_point_flux_mixed(col, st, n, ihn, ih1, ih2, G, dtf, Fn, dFn);
+                for (int n = 0; n < 2; n++) {
+                    const float ih2 = inv_metric_f(P, e2, P.my_gp, 2 * p[e2] + n);
+                    ff Fn[5];
+                    float dFn[5];
+                    gks_point_flux_mixed(col, st, n, ihn, ih1, ih2, G, dtf, Fn, dFn);
 #pragma unroll
-            for (int c = 0; c < 5; c++) {
-                Fs[c] = ff_add(Fs[c], ff_scale(Fn[c], 0.25f));  // Gauss weights 1/4 (exact)
-                dFs[c] += 0.25f * dFn[c];
+                    for (int c = 0; c < 5; c++) {
+                        Fs[c] = ff_add(Fs[c], ff_scale(Fn[c], 0.25f));  // Gauss weights 1/4 (exact)
+                        dFs[c] += 0.25f * dFn[c];
+                    }
+                }
             }
         }
+        __syncthreads();  // the buffer of this row type is refilled two iterations later
     }
+    if (!valid) return;
     double area;
-    if (d == 0) area = P.hy_cell[a] * P.h[2];
+    if (d == 0) area = P.hy_cell[p[1]] * P.h[2];
     else if (d == 1) area = P.h[0] * P.h[2];
-    else area = P.h[0] * P.hy_cell[b];
+    else area = P.h[0] * P.hy_cell[p[1]];
+    const long long t = blin(Bf, p);
 #pragma unroll
     for (int c = 0; c < 5; c++) {
         F[(long long)perm_mx(d, c) * nf + t] = ff_to_double(Fs[c]) * area;
