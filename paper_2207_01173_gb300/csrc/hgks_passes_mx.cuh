@@ -503,30 +503,34 @@ static __device__ __forceinline__ float inv_metric_f(const Params &P, int e, con
 }
 
 // ---------------------------------------------------------------------------
-// pass 3 on block tiles: 32 faces along x by 4 along the second tangential
-// direction e2 (one warp per e2 row).  The four e2 rows of a tile share the
-// eight t1 rows b0-2 .. b0+5 of every row type, so the block stages those in
-// shared memory once (8 instead of 20 row loads per 4 faces) and prefetches
-// the next row type with cp.async while it reduces the current one.
+// pass 3 on block tiles: 32 face columns by 4 positions along the second
+// tangential direction e2 (one warp per e2 position).  The columns are 32
+// consecutive (x, other-axis) pairs of the plane normal to e2, flattened so
+// that no lane idles at the end of an x row.  The four e2 positions of a tile
+// share the eight t1 rows b0-2 .. b0+5 of every row type, so the block stages
+// those in shared memory once (8 instead of 20 row loads per 4 faces) and
+// prefetches the next row type with cp.async while it reduces the current
+// one; each lane stages its own column.
 // ---------------------------------------------------------------------------
 constexpr int FT_X = 32, FT_B = 4, FT_ROWS = FT_B + 4;
 constexpr int FT_STAGE = 2 * 2 * FT_ROWS * FT_X;  // floats: [buffer][array][row][x]
 constexpr int FLUX_MX_TILE_SMEM = FLUX_MX_SMEM + FT_STAGE * (int)sizeof(float);
 
 struct FluxTiling {
-    int e2, other, nxt, nbt, no;
-    long long count;
+    int e2, other, E0, no, nbt;
+    long long ncol, ngt, count;  // columns (x, other) of the plane, column tiles, tiles
 };
 __host__ __device__ inline FluxTiling flux_tiling(const Params &P, int d)
 {
     FluxTiling f;
     f.e2 = tdir(d, 1);
     f.other = d == 2 ? 2 : 1;  // the axis that is neither x nor e2
-    const int E0 = P.n[0] + (d == 0 ? 1 : 0);
-    f.nxt = (E0 + FT_X - 1) / FT_X;
-    f.nbt = (P.n[f.e2] + FT_B - 1) / FT_B;
+    f.E0 = P.n[0] + (d == 0 ? 1 : 0);
     f.no = P.n[f.other] + (f.other == d ? 1 : 0);
-    f.count = (long long)f.nxt * f.nbt * f.no;
+    f.nbt = (P.n[f.e2] + FT_B - 1) / FT_B;
+    f.ncol = (long long)f.E0 * f.no;
+    f.ngt = (f.ncol + FT_X - 1) / FT_X;
+    f.count = f.ngt * f.nbt;
     return f;
 }
 
@@ -560,38 +564,37 @@ static __device__ __forceinline__ void flux_mx_tile(const Params &P, int d, cons
 {
     const FluxTiling ft = flux_tiling(P, d);
     const long long nf = box_count(Bf), nt = box_count(Bt);
-    const int xt = (int)(T % ft.nxt);
-    const long long r1 = T / ft.nxt;
-    const int bt = (int)(r1 % ft.nbt), o = (int)(r1 / ft.nbt);
-    const int x0 = xt * FT_X, b0 = bt * FT_B;
+    const long long gt = T % ft.ngt;
+    const int b0 = (int)(T / ft.ngt) * FT_B;
     const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
     const int e1 = tdir(d, 0), e2 = ft.e2;
-    // this thread's face
+    // this lane's column and this thread's face
+    const long long g = gt * FT_X + lane;
+    const bool col_ok = g < ft.ncol;
     int p[3];
-    p[0] = x0 + lane;
+    p[0] = col_ok ? (int)(g % ft.E0) : 0;
+    p[ft.other] = col_ok ? (int)(g / ft.E0) : 0;
     p[e2] = b0 + wb;
-    p[ft.other] = o;
-    const bool valid = p[0] < Bf.E[0] && p[e2] < Bf.E[e2];
-    // first t1 row of the tile (e2 index b0 - 2, x0) and the row stride
-    int q0[3] = { x0, 0, 0 };
+    const bool valid = col_ok && p[e2] < Bf.E[e2];
+    // this lane's first staged t1 row (e2 index b0 - 2) and the row stride
+    int q0[3] = { p[0], p[1], p[2] };
     q0[e2] = b0 - 2;
-    q0[ft.other] = o;
-    const long long base0 = blin(Bt, q0), s2 = bstride(Bt, e2);
-    const int xlim = Bf.E[0] - x0;            // lanes with x in range
-    const int rlim = P.n[e2] + 3 - b0;        // rows r with e2 index b0 - 2 + r <= n + 1
+    const long long base_l = blin(Bt, q0), s2 = bstride(Bt, e2);
+    const int rlim = P.n[e2] + 3 - b0;  // rows r with e2 index b0 - 2 + r <= n + 1
     float *gp = sm, *stage = sm + GP_SLOTS * FLUX_MX_BLOCK;
     const int st = blockDim.x;
     float *col = gp + threadIdx.x;
 
+    // cooperative staging: thread (lane, wb) copies rows wb, wb + 4 of both
+    // arrays for its lane's column (segments wb + 4 i, i = 0..3)
     auto issue = [&](int it) {
         const float *A, *B;
         ft_planes(in, nt, it, A, B);
         float *buf = stage + (it & 1) * (2 * FT_ROWS * FT_X);
 #pragma unroll
         for (int i = 0; i < (2 * FT_ROWS * FT_X) / FLUX_MX_BLOCK; i++) {
-            const int e = threadIdx.x + i * FLUX_MX_BLOCK;
-            const int seg = e >> 5, l = e & 31, arr = seg / FT_ROWS, r = seg % FT_ROWS;
-            if (l < xlim && r <= rlim) cp_async4(buf + e, (arr ? B : A) + base0 + r * s2 + l);
+            const int seg = wb + 4 * i, arr = seg / FT_ROWS, r = seg % FT_ROWS;
+            if (col_ok && r <= rlim) cp_async4(buf + seg * FT_X + lane, (arr ? B : A) + base_l + r * s2);
         }
         cp_async_commit();
     };
