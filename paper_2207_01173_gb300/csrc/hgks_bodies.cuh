@@ -105,9 +105,13 @@ struct FaceGeom {
 
 // second tangential direction, the four Gauss-point fluxes and their sum.
 // load(slot, j): first-pass slot at offset j - 2 along the second tangential
-// direction.  Fs, dFs: F^n and dF^n/dt times the face area, rotated frame.
+// direction.  col: scratch of 110 values for the inputs of the two Gauss
+// points of a line, laid out as the point flux reads them: for Gauss point n
+// at n * 55: Ql (5), Qr (5), then the physical slopes dl[3][5], dr[3][5],
+// d0[3][5] (normal, t1, t2).  Fs, dFs: F^n and dF^n/dt times the face area,
+// rotated frame.
 template <typename T, typename Load>
-HGKS_HD void flux_body(Load load, const FaceGeom &G, const Params &P, T dt, T Fs[5], T dFs[5])
+HGKS_HD void flux_body(Load load, const FaceGeom &G, const Params &P, T dt, T *col, T Fs[5], T dFs[5])
 {
 #pragma unroll
     for (int c = 0; c < 5; c++) {
@@ -117,7 +121,7 @@ HGKS_HD void flux_body(Load load, const FaceGeom &G, const Params &P, T dt, T Fs
 #pragma unroll 1
     for (int m = 0; m < 2; m++) {
         const double ih1 = G.ih1[m];
-        T gv[2][25], gd1[2][15], gd2[2][15];
+        // WENO to the Gauss points: values of Ql, Qr (rows 0..9), normal slopes (rows 10..24)
 #pragma unroll 1
         for (int k = 0; k < 25; k++) {
             T X[5];
@@ -125,37 +129,42 @@ HGKS_HD void flux_body(Load load, const FaceGeom &G, const Params &P, T dt, T Fs
             for (int j = 0; j < 5; j++) X[j] = load(m * 55 + k, j);
             WenoPrep<T> W;
             weno_prep(X, W);
-            weno_gauss_pair(W, gv[0][k], gv[1][k]);
+            T v0, v1;
+            weno_gauss_pair(W, v0, v1);
+            if (k < 10) {
+                col[k] = v0;
+                col[55 + k] = v1;
+            } else {
+                const int slot = k < 15 ? k : (k < 20 ? k + 10 : k + 20);  // dl/dr/d0[0][c]
+                col[slot] = v0 * T(G.ihn);
+                col[55 + slot] = v1 * T(G.ihn);
+            }
         }
+        // first-direction derivatives (quartic value) and second-direction derivatives
+        // of the first-direction quartic values (quartic derivative)
 #pragma unroll 1
         for (int k = 0; k < 15; k++) {
             T X[5], Y[5];
 #pragma unroll
             for (int j = 0; j < 5; j++) {
-                X[j] = load(m * 55 + 40 + k, j);  // first-direction derivatives
-                Y[j] = load(m * 55 + 25 + k, j);  // first-direction quartic values
+                X[j] = load(m * 55 + 40 + k, j);
+                Y[j] = load(m * 55 + 25 + k, j);
             }
-            quartic_value_pair(X, gd1[0][k], gd1[1][k]);
-            quartic_deriv_pair(Y, gd2[0][k], gd2[1][k]);
+            T a0, a1, b0, b1;
+            quartic_value_pair(X, a0, a1);
+            quartic_deriv_pair(Y, b0, b1);
+            const int slot = 10 + (k / 5) * 15 + k % 5;  // d[.][0][c] of state k / 5
+            col[slot + 5] = a0 * T(ih1);
+            col[55 + slot + 5] = a1 * T(ih1);
+            col[slot + 10] = b0 * T(G.ih2[0]);
+            col[55 + slot + 10] = b1 * T(G.ih2[1]);
         }
 #pragma unroll 1
         for (int n = 0; n < 2; n++) {
-            const double ih2 = G.ih2[n];
-            T dl[3][5], dr[3][5], d0[3][5];
-#pragma unroll
-            for (int c = 0; c < 5; c++) {
-                dl[0][c] = gv[n][10 + c] * T(G.ihn);
-                dr[0][c] = gv[n][15 + c] * T(G.ihn);
-                d0[0][c] = gv[n][20 + c] * T(G.ihn);
-                dl[1][c] = gd1[n][c] * T(ih1);
-                dr[1][c] = gd1[n][5 + c] * T(ih1);
-                d0[1][c] = gd1[n][10 + c] * T(ih1);
-                dl[2][c] = gd2[n][c] * T(ih2);
-                dr[2][c] = gd2[n][5 + c] * T(ih2);
-                d0[2][c] = gd2[n][10 + c] * T(ih2);
-            }
+            const T *g = col + 55 * n;
             T Fn[5], dFn[5];
-            gks_point_flux<T>(&gv[n][0], &gv[n][5], dl, dr, d0, P, dt, Fn, dFn);
+            gks_point_flux<T>(g, g + 5, (const T(*)[5])(g + 10), (const T(*)[5])(g + 25), (const T(*)[5])(g + 40), P,
+                              dt, Fn, dFn);
 #pragma unroll
             for (int c = 0; c < 5; c++) {
                 Fs[c] += T(0.25) * Fn[c];

@@ -97,8 +97,8 @@ extern "C" hgks_status hgks_flop_model(const hgks_grid *grid, hgks_precision pre
         G.ihn = 50.0;
         G.ih1[0] = G.ih1[1] = G.ih2[0] = G.ih2[1] = 50.0;
         G.area = 4e-4;
-        Num Fs[5], dFs[5];
-        flux_body<Num>(load, G, P, Num(1e-3), Fs, dFs);
+        Num Fs[5], dFs[5], col[110];
+        flux_body<Num>(load, G, P, Num(1e-3), col, Fs, dFs);
     }
     hgks_count::cur = nullptr;
 

@@ -88,79 +88,22 @@ static __device__ __forceinline__ void pos_flux(const Params &P, int d, const Bo
     const int e1 = tdir(d, 0), e2 = tdir(d, 1);
     const int f = p[d], a = p[e1], b = p[e2];
     const long long base = box_lin(Bt, p), s2 = box_stride(Bt, e2);
-    const double ihn = 1.0 / (d == 1 ? P.my_face[f] : P.h[d]);
-    double area;
-    if (d == 0) area = P.hy_cell[a] * P.h[2];
-    else if (d == 1) area = P.h[0] * P.h[2];
-    else area = P.h[0] * P.hy_cell[b];
-    double ih2[2];
-    for (int n = 0; n < 2; n++) ih2[n] = 1.0 / (e2 == 1 ? P.my_gp[2 * b + n] : P.h[e2]);
-    double *col = sm + threadIdx.x * FLUX_STRIDE;
+    FaceGeom G;
+    G.ihn = 1.0 / (d == 1 ? P.my_face[f] : P.h[d]);
+    if (d == 0) G.area = P.hy_cell[a] * P.h[2];
+    else if (d == 1) G.area = P.h[0] * P.h[2];
+    else G.area = P.h[0] * P.hy_cell[b];
+    for (int m = 0; m < 2; m++) {
+        G.ih1[m] = 1.0 / (e1 == 1 ? P.my_gp[2 * a + m] : P.h[e1]);
+        G.ih2[m] = 1.0 / (e2 == 1 ? P.my_gp[2 * b + m] : P.h[e2]);
+    }
     auto load = [&](int slot, int j) { return t1[slot * nt + base + (j - 2) * s2]; };
     double Fs[5], dFs[5];
+    flux_body<double>(load, G, P, dt, sm + threadIdx.x * FLUX_STRIDE, Fs, dFs);
 #pragma unroll
     for (int c = 0; c < 5; c++) {
-        Fs[c] = 0.0;
-        dFs[c] = 0.0;
-    }
-#pragma unroll 1
-    for (int m = 0; m < 2; m++) {
-        const double ih1 = 1.0 / (e1 == 1 ? P.my_gp[2 * a + m] : P.h[e1]);
-        // WENO to the Gauss points: values of Ql, Qr (rows 0..9), normal slopes (rows 10..24)
-#pragma unroll 1
-        for (int k = 0; k < 25; k++) {
-            double X[5];
-#pragma unroll
-            for (int j = 0; j < 5; j++) X[j] = load(m * 55 + k, j);
-            WenoPrep<double> W;
-            weno_prep(X, W);
-            double v0, v1;
-            weno_gauss_pair(W, v0, v1);
-            if (k < 10) {
-                col[k] = v0;
-                col[55 + k] = v1;
-            } else {
-                const int slot = k < 15 ? k : (k < 20 ? k + 10 : k + 20);  // dl/dr/d0[0][c]
-                col[slot] = v0 * ihn;
-                col[55 + slot] = v1 * ihn;
-            }
-        }
-        // first-direction derivatives (quartic value) and second-direction derivatives
-        // of the first-direction quartic values (quartic derivative)
-#pragma unroll 1
-        for (int k = 0; k < 15; k++) {
-            double X[5], Y[5];
-#pragma unroll
-            for (int j = 0; j < 5; j++) {
-                X[j] = load(m * 55 + 40 + k, j);
-                Y[j] = load(m * 55 + 25 + k, j);
-            }
-            double a0, a1, b0, b1;
-            quartic_value_pair(X, a0, a1);
-            quartic_deriv_pair(Y, b0, b1);
-            const int slot = 10 + (k / 5) * 15 + k % 5;  // d[.][0][c] of state k / 5
-            col[slot + 5] = a0 * ih1;
-            col[55 + slot + 5] = a1 * ih1;
-            col[slot + 10] = b0 * ih2[0];
-            col[55 + slot + 10] = b1 * ih2[1];
-        }
-#pragma unroll 1
-        for (int n = 0; n < 2; n++) {
-            const double *g = col + 55 * n;
-            double Fn[5], dFn[5];
-            gks_point_flux<double>(g, g + 5, (const double(*)[5])(g + 10), (const double(*)[5])(g + 25),
-                                   (const double(*)[5])(g + 40), P, dt, Fn, dFn);
-#pragma unroll
-            for (int c = 0; c < 5; c++) {
-                Fs[c] += 0.25 * Fn[c];
-                dFs[c] += 0.25 * dFn[c];
-            }
-        }
-    }
-#pragma unroll
-    for (int c = 0; c < 5; c++) {
-        F[(long long)perm_of(d, c) * nf + t] = Fs[c] * area;
-        F[(long long)(5 + perm_of(d, c)) * nf + t] = dFs[c] * area;
+        F[(long long)perm_of(d, c) * nf + t] = Fs[c];
+        F[(long long)(5 + perm_of(d, c)) * nf + t] = dFs[c];
     }
 }
 

@@ -69,3 +69,17 @@ def test_batch_workload_is_seeded_and_in_range():
         assert all(v in (24, 32, 48, 64, 96) for v in n)
         assert 0.1 <= Ma <= 0.5 and 400.0 <= Re <= 3200.0
     assert len({n for n, _, _ in a}) > 20  # uneven grids
+
+
+def test_flop_model_counts_the_kernel_arithmetic():
+    """The roofline's algorithmic flops come from running the kernels' own
+    templated arithmetic on the host with a counting scalar; the counts are a
+    property of the code (they change only when the arithmetic does)."""
+    from paper_2207_01173_gb300 import hgks
+    m = hgks.flop_model((256, 256, 256))
+    assert m["flux_per_face"] == 17446 and m["div_per_face_flux"] == 102 and m["special_per_face_flux"] == 32
+    assert m["normal_per_face"] == 1068 and m["tan1_per_pos"] == 2250
+    # a step: two stages x three directions of each pass plus the cell passes
+    faces = 257 * 256 * 256
+    assert 2 * 3 * m["flux_per_face"] * faces < m["per_step"] < 1.2 * 2 * 3 * (
+        m["flux_per_face"] * faces + m["tan1_per_pos"] * 257 * 256 * 260 + m["normal_per_face"] * 257 * 260 * 260)
