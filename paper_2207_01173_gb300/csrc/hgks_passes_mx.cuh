@@ -437,8 +437,9 @@ static __device__ __forceinline__ void pos_tan1_mx(const Params &P, int d, const
     int p[3];
     bpos(Bt, t, p);
     const long long base = blin(Bq, p), s1 = bstride(Bq, tdir(d, 0));
-    // values: Ql, Qr (WENO + quartic), Q0 (quartic)
-#pragma unroll 1
+    // values: Ql, Qr (WENO + quartic), Q0 (quartic); fully unrolled so that
+    // the loads of all fifteen rows are in flight together (latency-bound)
+#pragma unroll 3
     for (int v = 0; v < 3; v++) {
 #pragma unroll
         for (int c = 0; c < 5; c++) {
@@ -476,7 +477,7 @@ static __device__ __forceinline__ void pos_tan1_mx(const Params &P, int d, const
         }
     }
     // slopes: WENO-Z in FP32
-#pragma unroll 1
+#pragma unroll 3
     for (int w = 0; w < 3; w++) {
 #pragma unroll
         for (int c = 0; c < 5; c++) {
