@@ -132,8 +132,7 @@ __global__ void __launch_bounds__(128) kb_normal(const Inst *__restrict__ I, con
     }
 }
 
-template <bool MX>
-__global__ void __launch_bounds__(128, MX ? 4 : 1) kb_tan1(const Inst *__restrict__ I, const Tile *__restrict__ T, int ntiles,
+__global__ void __launch_bounds__(128) kb_tan1(const Inst *__restrict__ I, const Tile *__restrict__ T, int ntiles,
                                                int d)
 {
     for (int k = blockIdx.x; k < ntiles; k += gridDim.x) {
@@ -141,16 +140,46 @@ __global__ void __launch_bounds__(128, MX ? 4 : 1) kb_tan1(const Inst *__restric
         const Inst &in = I[tl.inst];
         if (in.ctl->flag) continue;
         const Box Bt = box_t1(in.P, d), Bq = box_fq(in.P, d);
-        if constexpr (MX) {
-            const FqMx fi = fq_mx(in.fq, box_count(Bq));
-            const T1Mx o = t1_mx(in.t1, box_count(Bt));
-            for (long long t = tl.start + threadIdx.x; t < tl.start + tl.count; t += blockDim.x)
-                pos_tan1_mx(in.P, d, Bt, Bq, fi, o, t);
-        } else {
-            for (long long t = tl.start + threadIdx.x; t < tl.start + tl.count; t += blockDim.x)
-                pos_tan1(in.P, d, Bt, Bq, in.fq, in.t1, t);
-        }
+        for (long long t = tl.start + threadIdx.x; t < tl.start + tl.count; t += blockDim.x)
+            pos_tan1(in.P, d, Bt, Bq, in.fq, in.t1, t);
     }
+}
+
+// The mixed tan1 pass, like the mixed flux pass, is not persistent: one block
+// per tile of MX_TILE positions, one per thread, with the tile's problem
+// constants read once into shared memory.  Under a persistent loop, or with
+// the constants held in registers, its fully unrolled rows spilled 800-1000
+// bytes per thread; this way they take 88 registers.
+constexpr int MX_TILE = 128;
+
+__global__ void __launch_bounds__(MX_TILE, 4) kb_tan1_mx(const Inst *__restrict__ I, const Tile *__restrict__ T,
+                                                         int ntiles, int d)
+{
+    // the tile's problem constants, read once into shared memory
+    struct TanArgs {
+        Box Bt, Bq;
+        FqMx in;
+        T1Mx o;
+        long long start, count;
+        int flag;
+    };
+    __shared__ TanArgs a;
+    const int k = blockIdx.x;
+    if (k >= ntiles) return;
+    if (threadIdx.x == 0) {
+        const Tile tl = T[k];
+        const Inst &in = I[tl.inst];
+        a.Bt = box_t1(in.P, d);
+        a.Bq = box_fq(in.P, d);
+        a.in = fq_mx(in.fq, box_count(a.Bq));
+        a.o = t1_mx(in.t1, box_count(a.Bt));
+        a.start = tl.start;
+        a.count = tl.count;
+        a.flag = in.ctl->flag;
+    }
+    __syncthreads();
+    if (a.flag || (long long)threadIdx.x >= a.count) return;
+    tan1_mx_rows(d, a.Bt, a.Bq, a.in.vh, a.in.vl, a.in.vs, a.o.th, a.o.tl, a.o.ts, a.start + threadIdx.x);
 }
 
 // The mixed flux pass is the one pass that is not persistent: it launches one
@@ -312,6 +341,7 @@ static hgks_status build_tiles(hgks_batch_t b)
                 if (mixed != b->inst[i].mixed) continue;
                 const Box B = pass == 0 ? box_fq(P, d) : pass == 1 ? box_t1(P, d) : box_face(P, d);
                 if (mixed && pass == 2) add(w, i, flux_tiling(P, d).count, 1);  // one entry per flux tile
+                else if (mixed && pass == 1) add(w, i, box_count(B), MX_TILE);   // one block per tile
                 else add(w, i, box_count(B), b->tile_sweep);
             }
         }
@@ -353,13 +383,13 @@ static void enqueue_batch_step(hgks_batch_t b, double cfl)
                 if (mx) {
                     kb_normal<true><<<pgrid(b->cnt[wn], b->bsweep[1][0]), 128, 0, st>>>(I, T(wn), b->cnt[wn], d,
                                                                                        stage);
-                    kb_tan1<true><<<pgrid(b->cnt[wt], b->bsweep[1][1]), 128, 0, st>>>(I, T(wt), b->cnt[wt], d);
+                    kb_tan1_mx<<<(unsigned)b->cnt[wt], MX_TILE, 0, st>>>(I, T(wt), b->cnt[wt], d);
                     kb_flux_mx<<<(unsigned)b->cnt[wf], FLUX_MX_BLOCK, FLUX_MX_TILE_SMEM, st>>>(I, T(wf), b->cnt[wf],
                                                                                               d);
                 } else {
                     kb_normal<false><<<pgrid(b->cnt[wn], b->bsweep[0][0]), 128, 0, st>>>(I, T(wn), b->cnt[wn], d,
                                                                                         stage);
-                    kb_tan1<false><<<pgrid(b->cnt[wt], b->bsweep[0][1]), 128, 0, st>>>(I, T(wt), b->cnt[wt], d);
+                    kb_tan1<<<pgrid(b->cnt[wt], b->bsweep[0][1]), 128, 0, st>>>(I, T(wt), b->cnt[wt], d);
                     kb_flux<<<pgrid(b->cnt[wf], b->bsweep[0][2]), FLUX_BLOCK, FLUX_SMEM, st>>>(I, T(wf), b->cnt[wf],
                                                                                               d);
                 }
@@ -436,11 +466,11 @@ extern "C" hgks_status hgks_batch_create(hgks_t *handles, int n, hgks_batch_t *o
     // persistent grids: as many blocks as stay resident
     int nb[2][3] = {};
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[0][0], kb_normal<false>, 128, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[0][1], kb_tan1<false>, 128, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[0][1], kb_tan1, 128, 0);
     cudaFuncSetAttribute((const void *)kb_flux, cudaFuncAttributeMaxDynamicSharedMemorySize, FLUX_SMEM);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[0][2], kb_flux, FLUX_BLOCK, FLUX_SMEM);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[1][0], kb_normal<true>, 128, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[1][1], kb_tan1<true>, 128, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[1][1], kb_tan1_mx, MX_TILE, 0);
     cudaFuncSetAttribute((const void *)kb_flux_mx, cudaFuncAttributeMaxDynamicSharedMemorySize, FLUX_MX_TILE_SMEM);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[1][2], kb_flux_mx, FLUX_MX_BLOCK, FLUX_MX_TILE_SMEM);
     for (int m = 0; m < 2; m++)

@@ -430,16 +430,20 @@ static __device__ __forceinline__ void pos_normal_mx(const Params &P, int d, con
 // ---------------------------------------------------------------------------
 // pass 2: first tangential direction
 // ---------------------------------------------------------------------------
-static __device__ __forceinline__ void pos_tan1_mx(const Params &P, int d, const Box &Bt, const Box &Bq, FqMx in,
-                                                   T1Mx o, long long t)
+// The row loops are fully unrolled: all rows' loads are in flight together
+// (the pass is latency-bound), and with every index a compile-time constant
+// the pass needs fewer registers than with a rolled loop (80 against 128).
+static __device__ __forceinline__ void tan1_mx_rows(int d, const Box &Bt, const Box &Bq,
+                                                    const float *__restrict__ vh, const float *__restrict__ vl,
+                                                    const float *__restrict__ vs, float *__restrict__ th,
+                                                    float *__restrict__ tl, float *__restrict__ ts, long long t)
 {
     const long long nt = box_count(Bt);
     int p[3];
     bpos(Bt, t, p);
     const long long base = blin(Bq, p), s1 = bstride(Bq, tdir(d, 0));
-    // values: Ql, Qr (WENO + quartic), Q0 (quartic); fully unrolled so that
-    // the loads of all fifteen rows are in flight together (latency-bound)
-#pragma unroll 3
+    // values: Ql, Qr (WENO + quartic), Q0 (quartic)
+#pragma unroll
     for (int v = 0; v < 3; v++) {
 #pragma unroll
         for (int c = 0; c < 5; c++) {
@@ -447,8 +451,8 @@ static __device__ __forceinline__ void pos_tan1_mx(const Params &P, int d, const
             float H[5], L[5], x[5];
 #pragma unroll
             for (int j = 0; j < 5; j++) {
-                H[j] = in.vh[off + (j - 2) * s1];
-                L[j] = in.vl[off + (j - 2) * s1];
+                H[j] = vh[off + (j - 2) * s1];
+                L[j] = vl[off + (j - 2) * s1];
             }
 #pragma unroll
             for (int j = 0; j < 5; j++) x[j] = ff_dev(H[j], L[j], H[2], L[2]);
@@ -459,29 +463,29 @@ static __device__ __forceinline__ void pos_tan1_mx(const Params &P, int d, const
                 float vm, vp;
                 weno_gauss_pair(W, vm, vp);
                 const ff am = ff_add_f(ctr, vm), ap = ff_add_f(ctr, vp);
-                o.th[(0 * 25 + v * 5 + c) * nt + t] = am.hi;
-                o.tl[(0 * 25 + v * 5 + c) * nt + t] = am.lo;
-                o.th[(1 * 25 + v * 5 + c) * nt + t] = ap.hi;
-                o.tl[(1 * 25 + v * 5 + c) * nt + t] = ap.lo;
+                th[(0 * 25 + v * 5 + c) * nt + t] = am.hi;
+                tl[(0 * 25 + v * 5 + c) * nt + t] = am.lo;
+                th[(1 * 25 + v * 5 + c) * nt + t] = ap.hi;
+                tl[(1 * 25 + v * 5 + c) * nt + t] = ap.lo;
             }
             float qm, qp, dm, dp;
             quartic_value_pair(x, qm, qp);
             quartic_deriv_pair(x, dm, dp);
             const ff bm = ff_add_f(ctr, qm), bp = ff_add_f(ctr, qp);
-            o.th[(0 * 25 + 10 + v * 5 + c) * nt + t] = bm.hi;
-            o.tl[(0 * 25 + 10 + v * 5 + c) * nt + t] = bm.lo;
-            o.th[(1 * 25 + 10 + v * 5 + c) * nt + t] = bp.hi;
-            o.tl[(1 * 25 + 10 + v * 5 + c) * nt + t] = bp.lo;
-            o.ts[(0 * 30 + 15 + v * 5 + c) * nt + t] = dm;
-            o.ts[(1 * 30 + 15 + v * 5 + c) * nt + t] = dp;
+            th[(0 * 25 + 10 + v * 5 + c) * nt + t] = bm.hi;
+            tl[(0 * 25 + 10 + v * 5 + c) * nt + t] = bm.lo;
+            th[(1 * 25 + 10 + v * 5 + c) * nt + t] = bp.hi;
+            tl[(1 * 25 + 10 + v * 5 + c) * nt + t] = bp.lo;
+            ts[(0 * 30 + 15 + v * 5 + c) * nt + t] = dm;
+            ts[(1 * 30 + 15 + v * 5 + c) * nt + t] = dp;
         }
     }
     // slopes: WENO-Z in FP32
-#pragma unroll 3
+#pragma unroll
     for (int w = 0; w < 3; w++) {
 #pragma unroll
         for (int c = 0; c < 5; c++) {
-            const float *src = in.vs + (long long)(w * 5 + c) * box_count(Bq) + base;
+            const float *src = vs + (long long)(w * 5 + c) * box_count(Bq) + base;
             float x[5];
 #pragma unroll
             for (int j = 0; j < 5; j++) x[j] = src[(j - 2) * s1];
@@ -489,10 +493,20 @@ static __device__ __forceinline__ void pos_tan1_mx(const Params &P, int d, const
             weno_prep(x, W);
             float vm, vp;
             weno_gauss_pair(W, vm, vp);
-            o.ts[(0 * 30 + w * 5 + c) * nt + t] = vm;
-            o.ts[(1 * 30 + w * 5 + c) * nt + t] = vp;
+            ts[(0 * 30 + w * 5 + c) * nt + t] = vm;
+            ts[(1 * 30 + w * 5 + c) * nt + t] = vp;
         }
     }
+}
+
+// the input and output planes never overlap: passing them as restricted
+// pointers lets the compiler move the loads of later rows ahead of the
+// stores of earlier ones
+static __device__ __forceinline__ void pos_tan1_mx(const Params &P, int d, const Box &Bt, const Box &Bq, FqMx in,
+                                                   T1Mx o, long long t)
+{
+    (void)P;
+    tan1_mx_rows(d, Bt, Bq, in.vh, in.vl, in.vs, o.th, o.tl, o.ts, t);
 }
 
 // ---------------------------------------------------------------------------
@@ -514,7 +528,8 @@ static __device__ __forceinline__ float inv_metric_f(const Params &P, int e, con
 // one; each lane stages its own column.
 // ---------------------------------------------------------------------------
 constexpr int FT_X = 32, FT_B = 4, FT_ROWS = FT_B + 4;
-constexpr int FT_STAGE = 2 * 2 * FT_ROWS * FT_X;  // floats: [buffer][array][row][x]
+constexpr int FT_TYPE = 2 * FT_ROWS * FT_X;     // floats of one row type: [array][row][x]
+constexpr int FT_STAGE = 2 * 2 * FT_TYPE;       // [buffer][two row types]
 constexpr int FLUX_MX_TILE_SMEM = FLUX_MX_SMEM + FT_STAGE * (int)sizeof(float);
 
 struct FluxTiling {
@@ -587,15 +602,20 @@ static __device__ __forceinline__ void flux_mx_tile(const Params &P, int d, cons
     float *col = gp + threadIdx.x;
 
     // cooperative staging: thread (lane, wb) copies rows wb, wb + 4 of both
-    // arrays for its lane's column (segments wb + 4 i, i = 0..3)
-    auto issue = [&](int it) {
-        const float *A, *B;
-        ft_planes(in, nt, it, A, B);
-        float *buf = stage + (it & 1) * (2 * FT_ROWS * FT_X);
+    // arrays for its lane's column (segments wb + 4 i, i = 0..3); a stage
+    // holds two row types
+    auto issue = [&](int pair) {
+        float *buf = stage + (pair & 1) * (2 * FT_TYPE);
 #pragma unroll
-        for (int i = 0; i < (2 * FT_ROWS * FT_X) / FLUX_MX_BLOCK; i++) {
-            const int seg = wb + 4 * i, arr = seg / FT_ROWS, r = seg % FT_ROWS;
-            if (col_ok && r <= rlim) cp_async4(buf + seg * FT_X + lane, (arr ? B : A) + base_l + r * s2);
+        for (int u = 0; u < 2; u++) {
+            const float *A, *B;
+            ft_planes(in, nt, 2 * pair + u, A, B);
+#pragma unroll
+            for (int i = 0; i < FT_TYPE / FLUX_MX_BLOCK; i++) {
+                const int seg = wb + 4 * i, arr = seg / FT_ROWS, r = seg % FT_ROWS;
+                if (col_ok && r <= rlim)
+                    cp_async4(buf + u * FT_TYPE + seg * FT_X + lane, (arr ? B : A) + base_l + r * s2);
+            }
         }
         cp_async_commit();
     };
@@ -610,58 +630,63 @@ static __device__ __forceinline__ void flux_mx_tile(const Params &P, int d, cons
         Fs[c] = ff{ 0.0f, 0.0f };
         dFs[c] = 0.0f;
     }
+    // reduce the staged rows of row type it into this thread's Gauss-point inputs
+    auto reduce = [&](const float *buf, int it) {
+        const int k = it % 40;
+        float X[5], Y[5];
+#pragma unroll
+        for (int j = 0; j < 5; j++) {
+            X[j] = buf[(0 * FT_ROWS + wb + j) * FT_X + lane];
+            Y[j] = buf[(1 * FT_ROWS + wb + j) * FT_X + lane];
+        }
+        if (k < 25) {  // float-float values: deviations about the centre row
+            float x[5];
+#pragma unroll
+            for (int j = 0; j < 5; j++) x[j] = ff_dev(X[j], Y[j], X[2], Y[2]);
+            if (k < 10) {
+                WenoPrep<float> W;
+                weno_prep(x, W);
+                float vm, vp;
+                weno_gauss_pair(W, vm, vp);
+                const ff g0 = ff_add_f(ff{ X[2], Y[2] }, vm), g1 = ff_add_f(ff{ X[2], Y[2] }, vp);
+                col[GP_VAL(0, k, 0) * st] = g0.hi;
+                col[GP_VAL(0, k, 1) * st] = g0.lo;
+                col[GP_VAL(1, k, 0) * st] = g1.hi;
+                col[GP_VAL(1, k, 1) * st] = g1.lo;
+            } else {
+                float dm, dp;
+                quartic_deriv_pair(x, dm, dp);
+                col[GP_S2(0, k - 10) * st] = dm;
+                col[GP_S2(1, k - 10) * st] = dp;
+            }
+        } else {  // normal slopes (WENO) and first-direction derivatives (quartic value)
+            WenoPrep<float> W;
+            weno_prep(X, W);
+            float s0, s1, q0v, q1v;
+            weno_gauss_pair(W, s0, s1);
+            quartic_value_pair(Y, q0v, q1v);
+            col[GP_SN(0, k - 25) * st] = s0;
+            col[GP_SN(1, k - 25) * st] = s1;
+            col[GP_S1(0, k - 25) * st] = q0v;
+            col[GP_S1(1, k - 25) * st] = q1v;
+        }
+    };
     issue(0);
 #pragma unroll 1
-    for (int it = 0; it < 80; it++) {
-        if (it + 1 < 80) {
-            issue(it + 1);
+    for (int pair = 0; pair < 40; pair++) {
+        if (pair + 1 < 40) {
+            issue(pair + 1);
             cp_async_wait<1>();
         } else {
             cp_async_wait<0>();
         }
         __syncthreads();
-        const float *buf = stage + (it & 1) * (2 * FT_ROWS * FT_X);
-        const int k = it % 40;
+        const float *buf = stage + (pair & 1) * (2 * FT_TYPE);
         if (valid) {
-            float X[5], Y[5];
-#pragma unroll
-            for (int j = 0; j < 5; j++) {
-                X[j] = buf[(0 * FT_ROWS + wb + j) * FT_X + lane];
-                Y[j] = buf[(1 * FT_ROWS + wb + j) * FT_X + lane];
-            }
-            if (k < 25) {  // float-float values: deviations about the centre row
-                float x[5];
-#pragma unroll
-                for (int j = 0; j < 5; j++) x[j] = ff_dev(X[j], Y[j], X[2], Y[2]);
-                if (k < 10) {
-                    WenoPrep<float> W;
-                    weno_prep(x, W);
-                    float vm, vp;
-                    weno_gauss_pair(W, vm, vp);
-                    const ff g0 = ff_add_f(ff{ X[2], Y[2] }, vm), g1 = ff_add_f(ff{ X[2], Y[2] }, vp);
-                    col[GP_VAL(0, k, 0) * st] = g0.hi;
-                    col[GP_VAL(0, k, 1) * st] = g0.lo;
-                    col[GP_VAL(1, k, 0) * st] = g1.hi;
-                    col[GP_VAL(1, k, 1) * st] = g1.lo;
-                } else {
-                    float dm, dp;
-                    quartic_deriv_pair(x, dm, dp);
-                    col[GP_S2(0, k - 10) * st] = dm;
-                    col[GP_S2(1, k - 10) * st] = dp;
-                }
-            } else {  // normal slopes (WENO) and first-direction derivatives (quartic value)
-                WenoPrep<float> W;
-                weno_prep(X, W);
-                float s0, s1, q0v, q1v;
-                weno_gauss_pair(W, s0, s1);
-                quartic_value_pair(Y, q0v, q1v);
-                col[GP_SN(0, k - 25) * st] = s0;
-                col[GP_SN(1, k - 25) * st] = s1;
-                col[GP_S1(0, k - 25) * st] = q0v;
-                col[GP_S1(1, k - 25) * st] = q1v;
-            }
-            if (k == 39) {  // all inputs of line m: the two Gauss-point fluxes
-                const int m = it / 40;
+            reduce(buf, 2 * pair);
+            reduce(buf + FT_TYPE, 2 * pair + 1);
+            if (pair % 20 == 19) {  // all inputs of line m: the two Gauss-point fluxes
+                const int m = pair / 20;
                 const float ih1 = inv_metric_f(P, e1, P.my_gp, 2 * p[e1] + m);
 #pragma unroll 1
                 for (int n = 0; n < 2; n++) {
@@ -677,7 +702,7 @@ static __device__ __forceinline__ void flux_mx_tile(const Params &P, int d, cons
                 }
             }
         }
-        __syncthreads();  // the buffer of this row type is refilled two iterations later
+        __syncthreads();  // this buffer is refilled two iterations later
     }
     if (!valid) return;
     double area;
