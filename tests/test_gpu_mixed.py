@@ -127,3 +127,20 @@ def test_mixed_rhs_odd_and_degenerate_grids(hg, oracle, n, seed):
     # amplifies it by |F| / |dF| (pressure-dominated fluxes).  A face left out
     # or written twice would show as an O(1) error.
     assert e < 1e-4 and ed < 1e-2
+
+
+def test_mixed_bad_state_is_reported_and_rolled_back(hg):
+    """A non-finite cell in a mixed-precision problem travels through the
+    split, the FP32 passes and the FP64 update, is caught by the stage check,
+    and leaves the state at the last completed step."""
+    n = (12, 10, 8)
+    g = hg.Solver(n, precision=hg.MIXED, **TGV_KW)
+    g.init_tgv(0.1, 1.0, 1.0)
+    g.step(1, 0.5)
+    q = g.get_state()
+    q[2, 3, 4, 5] = np.nan
+    g.set_state(q)
+    with pytest.raises(hg.HgksError) as e:
+        g.step(2, 0.5)
+    assert e.value.status == hg.HGKS_ERR_NONFINITE
+    assert np.array_equal(g.get_state(), q, equal_nan=True)
