@@ -246,6 +246,41 @@ def serve_leg(hg, args, capacity):
     return summ
 
 
+def run_histories(args):
+    """Kinetic energy and enstrophy after every step of the TGV 256^3 run in
+    FP64 and in mixed precision from the same initial field: the statistical
+    error of the mixed path over a longer run.  Prints one JSON line."""
+    import torch
+    import paper_2207_01173_gb300 as hg
+    n, K = args.n, args.histories
+    hist = {}
+    for name, prec in (("fp64", hg.FP64), ("mixed", hg.MIXED)):
+        sv = hg.Solver((n, n, n), precision=prec, **tgv_kwargs())
+        sv.init_tgv(MA, 1.0, 1.0)
+        rows = []
+        t0 = time.perf_counter()
+        for _ in range(K):
+            sv.step(1, CFL)
+            st = sv.stats()
+            rows.append((st["t"], st["Ek"], st["enstrophy"], st["eps_com"]))
+        torch.cuda.synchronize()
+        hist[name] = (np.array(rows), time.perf_counter() - t0)
+        sv.close()
+    a, b = hist["fp64"][0], hist["mixed"][0]
+    rel = np.abs(b[:, 1:] - a[:, 1:]) / np.abs(a[:, 1:])
+    every = max(1, K // 20)
+    line = {"mode": "histories", "workload": workload_config(n)["workload"], "steps": K,
+            "max_rel_diff": {"Ek": float(rel[:, 0].max()), "enstrophy": float(rel[:, 1].max()),
+                             "eps_com": float(rel[:, 2].max())},
+            "t_end": {"fp64": float(a[-1, 0]), "mixed": float(b[-1, 0])},
+            "wall_s": {"fp64": hist["fp64"][1], "mixed": hist["mixed"][1]},
+            "history": [{"step": i + 1, "t": float(a[i, 0]), "Ek": float(a[i, 1]), "enstrophy": float(a[i, 2]),
+                         "Ek_rel": float(rel[i, 0]), "enstrophy_rel": float(rel[i, 1])}
+                        for i in range(every - 1, K, every)]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -422,6 +457,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=12)
     ap.add_argument("--serve-budget-gb", type=float, default=96.0)
     ap.add_argument("--serve-chunk", type=int, default=8)
+    ap.add_argument("--histories", type=int, default=0,
+                    help="instead of the benchmark: K steps in FP64 and mixed, E_k / enstrophy after each")
     ap.add_argument("--serve-policy", choices=["fair", "srpt"], default="srpt")
     ap.add_argument("--serve-age", type=float, default=10.0,
                     help="srpt aging: remaining work is divided by 1 + wait / this many seconds")
@@ -438,6 +475,8 @@ def main():
         world = max(world, 1)
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.histories > 0:
+        return run_histories(args)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
