@@ -247,35 +247,46 @@ def serve_leg(hg, args, capacity):
 
 
 def run_histories(args):
-    """Kinetic energy and enstrophy after every step of the TGV 256^3 run in
-    FP64 and in mixed precision from the same initial field: the statistical
-    error of the mixed path over a longer run.  Prints one JSON line."""
+    """Statistics after every step of a run in FP64 and in mixed precision
+    from the same initial field: the statistical error of the mixed path over
+    a longer run.  --case tgv: the Taylor-Green vortex (E_k, enstrophy,
+    dissipation); --case channel: the channel (E_k, mean wall shear).  Prints
+    one JSON line."""
     import torch
     import paper_2207_01173_gb300 as hg
+    from paper_2207_01173_gb300 import workloads
     n, K = args.n, args.histories
+    keys = ("Ek", "enstrophy", "eps_com") if args.case == "tgv" else ("Ek", "wall_shear", "mass")
     hist = {}
     for name, prec in (("fp64", hg.FP64), ("mixed", hg.MIXED)):
-        sv = hg.Solver((n, n, n), precision=prec, **tgv_kwargs())
-        sv.init_tgv(MA, 1.0, 1.0)
+        if args.case == "tgv":
+            sv = hg.Solver((n, n, n), precision=prec, **tgv_kwargs())
+            sv.init_tgv(MA, 1.0, 1.0)
+        else:
+            sv = hg.Solver((n, n, n), precision=prec, **workloads.channel_solver_kwargs())
+            sv.init_channel(0.5, 0.1, 2800)
         rows = []
         t0 = time.perf_counter()
         for _ in range(K):
             sv.step(1, CFL)
             st = sv.stats()
-            rows.append((st["t"], st["Ek"], st["enstrophy"], st["eps_com"]))
+            rows.append([st["t"]] + [st[k] for k in keys])
         torch.cuda.synchronize()
         hist[name] = (np.array(rows), time.perf_counter() - t0)
         sv.close()
     a, b = hist["fp64"][0], hist["mixed"][0]
     rel = np.abs(b[:, 1:] - a[:, 1:]) / np.abs(a[:, 1:])
     every = max(1, K // 20)
-    line = {"mode": "histories", "workload": workload_config(n)["workload"], "steps": K,
-            "max_rel_diff": {"Ek": float(rel[:, 0].max()), "enstrophy": float(rel[:, 1].max()),
-                             "eps_com": float(rel[:, 2].max())},
+    workload = (workload_config(n)["workload"] if args.case == "tgv" else
+                "channel %d^3, Ma_b 0.5, Re_b 2800, 2pi x 2 x pi, tanh-stretched y (b 2), isothermal walls, body "
+                "force (180/2800)^2, 10%% seeded velocity noise, CFL %.1f" % (n, CFL))
+    line = {"mode": "histories", "case": args.case, "workload": workload, "steps": K,
+            "max_rel_diff": {k: float(rel[:, i].max()) for i, k in enumerate(keys)},
             "t_end": {"fp64": float(a[-1, 0]), "mixed": float(b[-1, 0])},
             "wall_s": {"fp64": hist["fp64"][1], "mixed": hist["mixed"][1]},
-            "history": [{"step": i + 1, "t": float(a[i, 0]), "Ek": float(a[i, 1]), "enstrophy": float(a[i, 2]),
-                         "Ek_rel": float(rel[i, 0]), "enstrophy_rel": float(rel[i, 1])}
+            "history": [dict({"step": i + 1, "t": float(a[i, 0])},
+                             **{k: float(a[i, j + 1]) for j, k in enumerate(keys)},
+                             **{k + "_rel": float(rel[i, j]) for j, k in enumerate(keys)})
                         for i in range(every - 1, K, every)]}
     print(json.dumps(line), flush=True)
     return 0
@@ -458,7 +469,8 @@ def main():
     ap.add_argument("--serve-budget-gb", type=float, default=96.0)
     ap.add_argument("--serve-chunk", type=int, default=8)
     ap.add_argument("--histories", type=int, default=0,
-                    help="instead of the benchmark: K steps in FP64 and mixed, E_k / enstrophy after each")
+                    help="instead of the benchmark: K steps in FP64 and mixed, statistics after each")
+    ap.add_argument("--case", choices=["tgv", "channel"], default="tgv", help="problem of --histories")
     ap.add_argument("--serve-policy", choices=["fair", "srpt"], default="srpt")
     ap.add_argument("--serve-age", type=float, default=10.0,
                     help="srpt aging: remaining work is divided by 1 + wait / this many seconds")
