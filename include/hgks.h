@@ -56,10 +56,13 @@ typedef enum {
 
 typedef enum { HGKS_BC_PERIODIC = 0, HGKS_BC_ISOTHERMAL_WALL = 1 } hgks_bc;
 typedef enum { HGKS_VISC_CONSTANT = 0, HGKS_VISC_POWER = 1 } hgks_visc_kind;
-/* HGKS_FP64: all arithmetic in FP64.  HGKS_MIXED: reconstruction and flux
- * arithmetic in FP32 on deviations from FP64 centre values; FP64 for the
- * state, the stage update, the equilibrium state Q0 (mean of the two sides
- * plus an FP32 compatibility correction), its pressure and Euler flux. */
+/* HGKS_FP64: all arithmetic in FP64.  HGKS_MIXED: FP64 for the state and
+ * the stage update; reconstruction and flux arithmetic in FP32 on deviations
+ * from the stencil centre; the reconstructed values, the equilibrium state
+ * Q0 (mean of the two sides plus an FP32 compatibility correction), its
+ * pressure and Euler flux as float-float pairs (two FP32 numbers, ~48 bits).
+ * A MIXED handle allocates one more state-sized buffer (the state split into
+ * hi / lo FP32 planes before each stage). */
 typedef enum { HGKS_FP64 = 0, HGKS_MIXED = 1 } hgks_precision;
 
 /* Structured grid (Sec. 2 "orthogonal structured mesh"; Sec. 4.2 mesh map).
@@ -188,6 +191,10 @@ typedef struct {
     double special_per_face_flux; /* sqrt / exp / erfc / pow inside flux_per_face */
     double per_step;              /* all passes of one two-stage step on the grid */
 } hgks_flop_model_t;
+/* precision: HGKS_FP64 (the method's arithmetic; the mixed path runs the same
+ * formulas, with some values carried as float-float pairs on top, and is
+ * rejected here with INVALID_ARG).  Errors: INVALID_ARG (NULL, bad sizes,
+ * precision other than FP64). */
 hgks_status hgks_flop_model(const hgks_grid *grid, hgks_precision precision, hgks_flop_model_t *out);
 
 /* Largest grid (cells) accepted by hgks_cfl_dt_noalloc. */
