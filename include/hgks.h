@@ -293,8 +293,9 @@ void hgks_batch_destroy(hgks_batch_t b);
 /* Device bytes a handle for this grid and precision allocates (admission). */
 size_t hgks_footprint_bytes(const hgks_grid *grid, hgks_precision precision);
 
-/* Message of the last error on this handle (or a global message for
- * h == NULL).  Valid until the next call on the handle. */
+/* Message of the last error on this handle, or for h == NULL the last error
+ * of a call without a handle made on the calling thread.  Valid until the
+ * next call on the handle (or on the thread). */
 const char *hgks_last_error(hgks_t h);
 
 /* Wait for all work of the handle's stream. */

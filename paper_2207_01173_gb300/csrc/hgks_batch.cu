@@ -461,22 +461,36 @@ extern "C" hgks_status hgks_batch_create(hgks_t *handles, int n, hgks_batch_t *o
         b->inst.push_back(in);
     }
     int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
-    // persistent grids: as many blocks as stay resident
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                   cudaSuccess) {
+        cudaGetLastError();
+        set_global_error("hgks_batch_create: no usable CUDA device");
+        delete b;
+        return HGKS_ERR_CUDA;
+    }
+    // persistent grids: as many blocks as stay resident (the dynamic shared
+    // memory of the flux kernels needs the opt-in first)
     int nb[2][3] = {};
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[0][0], kb_normal<false>, 128, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[0][1], kb_tan1, 128, 0);
-    cudaFuncSetAttribute((const void *)kb_flux, cudaFuncAttributeMaxDynamicSharedMemorySize, FLUX_SMEM);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[0][2], kb_flux, FLUX_BLOCK, FLUX_SMEM);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[1][0], kb_normal<true>, 128, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[1][1], kb_tan1_mx, MX_TILE, 0);
-    cudaFuncSetAttribute((const void *)kb_flux_mx, cudaFuncAttributeMaxDynamicSharedMemorySize, FLUX_MX_TILE_SMEM);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[1][2], kb_flux_mx, FLUX_MX_BLOCK, FLUX_MX_TILE_SMEM);
+    cudaError_t e = cudaFuncSetAttribute((const void *)kb_flux, cudaFuncAttributeMaxDynamicSharedMemorySize, FLUX_SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute((const void *)kb_flux_mx, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 FLUX_MX_TILE_SMEM);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[0][0], kb_normal<false>, 128, 0);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[0][1], kb_tan1, 128, 0);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[0][2], kb_flux, FLUX_BLOCK, FLUX_SMEM);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[1][0], kb_normal<true>, 128, 0);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[1][1], kb_tan1_mx, MX_TILE, 0);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb[1][2], kb_flux_mx, FLUX_MX_BLOCK, FLUX_MX_TILE_SMEM);
+    if (e != cudaSuccess) {
+        set_global_error((std::string("hgks_batch_create: kernel set-up: ") + cudaGetErrorString(e)).c_str());
+        delete b;
+        return HGKS_ERR_CUDA;
+    }
     for (int m = 0; m < 2; m++)
         for (int p = 0; p < 3; p++) b->bsweep[m][p] = std::max(1, nb[m][p]) * b->sms;
     b->blocks_cells = b->sms * 8;
-    cudaError_t e = cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking);
+    e = cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev[0]);
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev[1]);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_inst, n * sizeof(Inst));
