@@ -9,6 +9,8 @@ CASES = {
     # name: (grid, slab sizes, solver kwargs, init, steps)
     "tgv_uneven": ((8, 6, 12), (8, 4), dict(visc=(1, 1.0 / 1600, 1.0 / (1.4 * 0.01), 0.7), Pr=0.72),
                    ("tgv", 0.1), 3),
+    "tgv_three": ((6, 5, 12), (3, 5, 4), dict(visc=(1, 1.0 / 1600, 1.0 / (1.4 * 0.01), 0.7), Pr=0.72),
+                  ("tgv", 0.1), 2),
     "channel": ((6, 16, 8), (4, 4), dict(lengths=(2.0, 2.0, 1.0), origin=(0.0, -1.0, 0.0), y_stretch_b=1.5,
                                          visc=(1, 1.0 / 2800, 1.0 / (1.4 * 0.25), 0.7), Pr=0.72,
                                          bc_lo=(0, 1, 0), bc_hi=(0, 1, 0), T_wall=1.0 / (1.4 * 0.25),
