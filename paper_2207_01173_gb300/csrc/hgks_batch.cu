@@ -29,7 +29,7 @@ void set_global_error(const char *msg);  // hgks_api.cu
 struct Inst {
     Params P;
     double *q[2], *qs, *r, *fq, *t1, *F[3];
-    float *qh, *ql;  // mixed: the split state
+    float2 *q2;  // mixed: the split state
     Ctl *ctl;
     int mixed, walls;
     double lxlz;
@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(256) kb_split(const Inst *__restrict__ I, cons
         if (in.ctl->flag) continue;
         const double *q = stage == 0 ? in.q[in.ctl->good] : in.qs;
         for (long long t = tl.start + threadIdx.x; t < tl.start + tl.count; t += blockDim.x)
-            pos_split_mx(in.P, q, in.qh, in.ql, t);
+            pos_split_mx(in.P, q, in.q2, t);
     }
 }
 
@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(128) kb_normal(const Inst *__restrict__ I, con
         if constexpr (MX) {
             const FqMx o = fq_mx(in.fq, box_count(B));
             for (long long t = tl.start + threadIdx.x; t < tl.start + tl.count; t += blockDim.x)
-                pos_normal_mx(in.P, d, B, in.qh, in.ql, o, t);
+                pos_normal_mx(in.P, d, B, in.q2, o, t);
         } else {
             for (long long t = tl.start + threadIdx.x; t < tl.start + tl.count; t += blockDim.x)
                 pos_normal(in.P, d, B, q, in.fq, t);
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(MX_TILE, 4) kb_tan1_mx(const Inst *__restrict_
     }
     __syncthreads();
     if (a.flag || (long long)threadIdx.x >= a.count) return;
-    tan1_mx_rows(d, a.Bt, a.Bq, a.in.vh, a.in.vl, a.in.vs, a.o.th, a.o.tl, a.o.ts, a.start + threadIdx.x);
+    tan1_mx_rows(d, a.Bt, a.Bq, a.in.v, a.in.vs, a.o.th, a.o.tl, a.o.ts, a.start + threadIdx.x);
 }
 
 // The mixed flux pass is the one pass that is not persistent: it launches one
@@ -453,8 +453,7 @@ extern "C" hgks_status hgks_batch_create(hgks_t *handles, int n, hgks_batch_t *o
         for (int d = 0; d < 3; d++) in.F[d] = h->F[d];
         in.ctl = h->ctl;
         in.mixed = h->prec == HGKS_MIXED;
-        in.qh = (float *)h->qf;
-        in.ql = in.qh ? in.qh + 5 * h->P.cs : nullptr;
+        in.q2 = (float2 *)h->qf;
         in.walls = h->P.bc_lo[1] == HGKS_BC_ISOTHERMAL_WALL || h->P.bc_hi[1] == HGKS_BC_ISOTHERMAL_WALL;
         in.lxlz = h->grid.lx * h->grid.lz;
         b->any_walls |= in.walls != 0;

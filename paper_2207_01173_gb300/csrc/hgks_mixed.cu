@@ -4,20 +4,20 @@
 
 namespace hgks {
 
-__global__ void __launch_bounds__(256) k_split_mx(Params P, const double *__restrict__ q, float *__restrict__ qh,
-                                                  float *__restrict__ ql, const Ctl *__restrict__ ctl)
+__global__ void __launch_bounds__(256) k_split_mx(Params P, const double *__restrict__ q, float2 *__restrict__ q2,
+                                                  const Ctl *__restrict__ ctl)
 {
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= P.cs || ctl->flag) return;
-    pos_split_mx(P, q, qh, ql, t);
+    pos_split_mx(P, q, q2, t);
 }
 
-__global__ void __launch_bounds__(128) k_normal_mx(Params P, int d, Box B, const float *__restrict__ qh,
-                                                   const float *__restrict__ ql, FqMx o, const Ctl *__restrict__ ctl)
+__global__ void __launch_bounds__(128) k_normal_mx(Params P, int d, Box B, const float2 *__restrict__ q2, FqMx o,
+                                                   const Ctl *__restrict__ ctl)
 {
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= box_count(B) || ctl->flag) return;
-    pos_normal_mx(P, d, B, qh, ql, o, t);
+    pos_normal_mx(P, d, B, q2, o, t);
 }
 
 __global__ void __launch_bounds__(128, 4) k_tan1_mx(Params P, int d, Box Bt, Box Bq, FqMx in, T1Mx o,
@@ -50,11 +50,10 @@ cudaError_t mixed_setup()
 
 static inline unsigned gridx(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
-// qf holds the split state: 5 hi planes then 5 lo planes of cs floats
+// qf holds the split state: 5 planes of cs (hi, lo) float pairs
 void launch_split_mixed(const Params &P, const double *q, double *qf, const Ctl *ctl, cudaStream_t st)
 {
-    float *qh = (float *)qf;
-    k_split_mx<<<gridx(P.cs, 256), 256, 0, st>>>(P, q, qh, qh + 5 * P.cs, ctl);
+    k_split_mx<<<gridx(P.cs, 256), 256, 0, st>>>(P, q, (float2 *)qf, ctl);
 }
 
 // the FP64-sized fq / t1 buffers hold the float planes of the mixed passes
@@ -63,8 +62,7 @@ void launch_sweep_mixed(const Params &P, int d, const double *qf, double *fq, do
 {
     Box Bq = box_fq(P, d), Bt = box_t1(P, d), Bf = box_face(P, d);
     const long long nq = box_count(Bq), nt = box_count(Bt);
-    const float *qh = (const float *)qf;
-    if (which == 0) k_normal_mx<<<gridx(nq, 128), 128, 0, st>>>(P, d, Bq, qh, qh + 5 * P.cs, fq_mx(fq, nq), ctl);
+    if (which == 0) k_normal_mx<<<gridx(nq, 128), 128, 0, st>>>(P, d, Bq, (const float2 *)qf, fq_mx(fq, nq), ctl);
     else if (which == 1) k_tan1_mx<<<gridx(nt, 128), 128, 0, st>>>(P, d, Bt, Bq, fq_mx(fq, nq), t1_mx(t1, nt), ctl);
     else
         k_flux_mx<<<(unsigned)flux_tiling(P, d).count, FLUX_MX_BLOCK, FLUX_MX_TILE_SMEM, st>>>(P, d, Bf, Bt,
