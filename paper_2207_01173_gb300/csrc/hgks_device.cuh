@@ -24,6 +24,24 @@
 
 #define HGKS_HD __host__ __device__ __forceinline__
 
+// Reciprocal of the WENO weight normaliser.  In FP32 (the mixed path) the
+// approximate reciprocal (at most 2 ulp) is enough: it scales a deviation
+// from the stencil centre, so it moves the reconstruction by ~1e-7 of a
+// deviation, never the centre value, and consistency (weights summing to one)
+// is exact because numerator and denominator share it.  FP64 divides.
+template <typename T>
+__host__ __device__ __forceinline__ T weno_recip(T x)
+{
+    return T(1.0) / x;
+}
+#ifdef __CUDA_ARCH__
+template <>
+__device__ __forceinline__ float weno_recip<float>(float x)
+{
+    return __fdividef(1.0f, x);
+}
+#endif
+
 namespace hgks {
 
 constexpr int NG = 3;            // ghost layers (fifth-order WENO needs three)
@@ -123,7 +141,7 @@ HGKS_HD void weno_gauss_pair(const WenoPrep<T> &W, T &vm, T &vp)
     const T dp = e0 + a1 + e2, dm = f0 + a1 + f2;  // plus: (DGL, DGC, DGR), minus: mirrored
     const T np = e0 * W.c1[0] + a1 * W.c1[1] + e2 * W.c1[2];
     const T nm = f0 * W.c1[0] + a1 * W.c1[1] + f2 * W.c1[2];
-    const T r = T(1.0) / (dp * dm);
+    const T r = weno_recip<T>(dp * dm);
     vp = W.x0 + T(HGKS_GAUSS) * (np * dm * r);
     vm = W.x0 - T(HGKS_GAUSS) * (nm * dp * r);
 }
@@ -140,7 +158,7 @@ HGKS_HD void weno_edge_pair(const WenoPrep<T> &W, T &vl, T &vr)
     const T nr = r0 * (p0 + h * W.c1[0]) + a1 * (p1 + h * W.c1[1]) + r2 * (p2 + h * W.c1[2]);
     const T nl = l0 * (p0 - h * W.c1[0]) + a1 * (p1 - h * W.c1[1]) + l2 * (p2 - h * W.c1[2]);
     const T dr = r0 + a1 + r2, dl = l0 + a1 + l2;
-    const T r = T(1.0) / (dr * dl);
+    const T r = weno_recip<T>(dr * dl);
     vr = nr * dl * r;
     vl = nl * dr * r;
 }
