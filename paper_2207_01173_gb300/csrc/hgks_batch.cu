@@ -634,6 +634,7 @@ extern "C" hgks_status hgks_batch_tune(hgks_batch_t b, double cfl, double *best_
     };
     const long long cand[] = { 256, 1024, 4096, 16384 };
     double best = 1e300;
+    const long long old_ts = b->tile_sweep;
     long long best_ts = b->tile_sweep;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
@@ -663,8 +664,12 @@ extern "C" hgks_status hgks_batch_tune(hgks_batch_t b, double cfl, double *best_
     cudaError_t r = restore();
     for (int i = 0; i < n; i++)
         if (saved[i]) cudaFree(saved[i]);
-    if (e != cudaSuccess || r != cudaSuccess)
-        return berr(b, HGKS_ERR_CUDA, std::string("tuning: ") + cudaGetErrorString(e != cudaSuccess ? e : r));
+    if (e != cudaSuccess || r != cudaSuccess) {
+        const std::string msg = std::string("tuning: ") + cudaGetErrorString(e != cudaSuccess ? e : r);
+        b->tile_sweep = old_ts;  // back to the tiling the batch had
+        build_tiles(b);
+        return berr(b, HGKS_ERR_CUDA, msg);
+    }
     b->tile_sweep = best_ts;
     hgks_status s = build_tiles(b);
     if (s) return s;

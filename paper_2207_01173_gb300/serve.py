@@ -67,17 +67,21 @@ class CudaEngine:
 
     def step(self, handles, nsteps):
         """Advance all handles nsteps; returns the step counters after."""
-        if tuple(handles) != self.members:
-            self._drop_batch()
-            self.batch = hgks.Batch(handles)
-            self.members = tuple(handles)
-            self.rebuilds += 1
         try:
-            self.batch.step(nsteps, self.cfl)
+            if tuple(handles) != self.members:
+                self._drop_batch()
+                self.batch = hgks.Batch(handles)
+                self.members = tuple(handles)
+                self.rebuilds += 1
+            try:
+                self.batch.step(nsteps, self.cfl)
+            except hgks.HgksError as e:
+                if e.status != hgks.HGKS_ERR_NONFINITE:
+                    raise
+            return self.batch.steps()
         except hgks.HgksError as e:
-            if e.status != hgks.HGKS_ERR_NONFINITE:
-                raise
-        return self.batch.steps()
+            self._drop_batch()
+            raise EngineError(str(e)) from e
 
     def result(self, h, keep_state=False):
         st = h.stats()
@@ -188,7 +192,14 @@ class Server:
             ids = self._working_set(running, now)
             chunk = min(self.max_chunk, min(running[i]["req"]["steps"] - running[i]["done"] for i in ids))
             c0 = self.clock()
-            counts = self.engine.step([running[i]["h"] for i in ids], chunk)
+            try:
+                counts = self.engine.step([running[i]["h"] for i in ids], chunk)
+            except EngineError as e:
+                # the batch step itself failed: its requests fail, the others go on
+                now = self.clock() - t0
+                for i in ids:
+                    retire(i, "failed", now, error="batch step failed: %s" % e)
+                continue
             conc.append((self.clock() - c0, len(ids)))
             chunks += 1
             now = self.clock() - t0

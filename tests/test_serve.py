@@ -34,11 +34,14 @@ class FakeEngine:
     def create(self, req):
         if req.get("fail_create"):
             raise EngineError("injected create failure")
-        h = dict(id=req["id"], cells=int(np.prod(req["n"])), step=0, bad_at=req.get("bad_at"))
+        h = dict(id=req["id"], cells=int(np.prod(req["n"])), step=0, bad_at=req.get("bad_at"),
+                 poison=req.get("poison", False))
         self.live[req["id"]] = h
         return req["id"]
 
     def step(self, handles, nsteps):
+        if any(self.live[h].get("poison") for h in handles):
+            raise EngineError("injected batch failure")
         self.steps_log.append((tuple(handles), nsteps))
         self.clock.t += nsteps * sum(self.live[h]["cells"] for h in handles) * 1e-6
         out = []
@@ -177,3 +180,16 @@ def test_srpt_aging_lets_a_long_waiting_request_in():
         done[age] = (res[1]["t_done"], last_small)
     assert done[0.0][0] > done[0.0][1]    # pure SRPT: after the whole stream
     assert done[0.05][0] < done[0.05][1]  # aging: before the stream ends
+
+
+def test_failed_batch_step_fails_its_working_set_only():
+    # request 1 makes every batch it is in fail; under "srpt" with a small
+    # fill target the other requests run in working sets of their own
+    reqs = [req(0, 0.0, 10, 6), req(1, 0.0, 20, 6, poison=True), req(2, 0.5, 10, 6)]
+    clk = FakeClock()
+    eng = FakeEngine(clk)
+    srv = Server(eng, 10 ** 9, max_chunk=8, clock=clk, sleep=clk.sleep, policy="srpt", fill_cells=1)
+    res, summ = srv.run(reqs)
+    assert res[1]["status"] == "failed" and "injected batch failure" in res[1]["error"]
+    assert res[0]["status"] == res[2]["status"] == "done"
+    assert 1 in eng.released and not eng.live
