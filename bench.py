@@ -4,10 +4,23 @@ CFL 0.5), synthetic data (the exact-average TGV initial field).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--n 256]
 
-Prints one JSON line (rank 0).  With N > 1 (torchrun, one process per GPU)
-every rank advances its own independent replica of the problem (the
-single-GPU method does not shard); value is the total over ranks and the
-time is the maximum over ranks.
+Prints one JSON line (rank 0).  Besides the FP64 headline (`value`, its
+roofline and an end-to-end figure through host buffers) the line carries:
+  mixed    - the same workload in mixed precision, with its error against
+             the FP64 run and a roofline against the FP32 pipe;
+  batched  - 64 Taylor-Green problems on uneven grids, stepped one by one and
+             as one batch (--batch-steps), FP64 and mixed;
+  serve    - the first --serve-requests requests of the seeded 500-request
+             stream through the continuous-batching serve loop;
+  cpu_baseline - the CPU oracle on a bounded sample (TGV 32^3).
+With N > 1 (torchrun, one process per GPU) every rank advances its own
+independent replica (the slab decomposition is host logic tested on CPU
+ranks; one GPU per run here); value is the total over ranks and the time is
+the maximum over ranks.
+
+--histories K runs K steps in FP64 and in mixed precision from the same
+field instead and prints the statistics after every step (--case tgv or
+channel).
 
 --impl reference times the CPU oracle (test infrastructure, the paper's
 method written out plainly in C) on this machine's host cores, on a bounded
