@@ -48,6 +48,8 @@ METRIC = "cell-updates/s TGV 256^3 FP64 vs mixed at stated error; serve p50/p99 
 # 278.7 MB for 266,240 faces); scaled by the faces of a launch.  Must be
 # re-measured whenever k_flux changes.
 K_FLUX_DRAM_BYTES_PER_FACE = 278708480 / 266240
+# the same for k_flux_mx (196.4 MB for 266,240 faces of TGV 64^3)
+K_FLUX_MX_DRAM_BYTES_PER_FACE = 196355328 / 266240
 # GB300 FP32 (non-tensor) peak: 152 SMs x 128 FP32 lanes x 2 flops per FMA x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # Table 3 of the paper: 256^3 TGV, FP64, Tesla V100, 11.697 h for 20 t_c at dt = 8.925e-4
@@ -390,7 +392,9 @@ def run_ours(args, rank, world, local_rank):
         fl_flops = model["flux_per_face"] * (n + 1) * n * n
         ach = fl_flops / (fl_ms * 1e-3) / 1e12
         mixed["roofline"] = {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                             "frac": ach / FP32_PEAK_TFLOPS, "traffic": None, "kernel": "k_flux_mx",
+                             "frac": ach / FP32_PEAK_TFLOPS, "traffic": K_FLUX_MX_DRAM_BYTES_PER_FACE * (n + 1) * n * n,
+                             "traffic_note": "ncu DRAM bytes of one TGV 64^3 launch scaled by faces",
+                             "kernel": "k_flux_mx",
                              "peak_note": "FP32 FMA peak from unit counts and clock: 152 SMs x 128 lanes x 2 "
                                           "flops x 2.07 GHz",
                              "algorithmic_flops_per_launch": fl_flops, "avg_launch_ms": fl_ms}
