@@ -145,6 +145,24 @@ def oracle_threads():
     return int(v) if v else os.cpu_count()
 
 
+def host_cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the baseline line."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -158,7 +176,7 @@ def run_reference(args, rank, world):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(args.n),
             "cpu_baseline": {"value": rate, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
-                             "sample": sample},
+                             "cpu_model": host_cpu_model(), "sample": sample},
             "e2e": {"value": rate, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -316,6 +334,7 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, el = oracle_rate(args.cpu_steps, args.ref_n)
         cpu_baseline = {"value": rate, "unit": "cell-updates/s", "cores": oracle_threads(), "kind": "oracle",
+                        "cpu_model": host_cpu_model(),
                         "sample": "TGV %d^3, %d steps after 1 untimed (same per-cell work as %d^3), %.1f s"
                                   % (args.ref_n, args.cpu_steps, args.n, el)}
 
