@@ -299,13 +299,21 @@ def run_histories(args):
             sv = hg.Solver((n, n, n), precision=prec, **workloads.channel_solver_kwargs())
             sv.init_channel(0.5, 0.1, 2800)
         rows = []
+        prof, nprof = None, 0
         t0 = time.perf_counter()
-        for _ in range(K):
+        for i in range(K):
             sv.step(1, CFL)
             st = sv.stats()
             rows.append([st["t"]] + [st[k] for k in keys])
+            if args.case == "channel" and i >= K - K // 4:
+                # mean streamwise velocity profile <rho u> / <rho> over x and z,
+                # averaged over the last quarter of the run (a host diagnostic)
+                q = sv.get_state()
+                u = q[1].mean(axis=(0, 2)) / q[0].mean(axis=(0, 2))
+                prof = u if prof is None else prof + u
+                nprof += 1
         torch.cuda.synchronize()
-        hist[name] = (np.array(rows), time.perf_counter() - t0)
+        hist[name] = (np.array(rows), time.perf_counter() - t0, None if prof is None else prof / nprof)
         sv.close()
     a, b = hist["fp64"][0], hist["mixed"][0]
     rel = np.abs(b[:, 1:] - a[:, 1:]) / np.abs(a[:, 1:])
@@ -321,6 +329,12 @@ def run_histories(args):
                              **{k: float(a[i, j + 1]) for j, k in enumerate(keys)},
                              **{k + "_rel": float(rel[i, j]) for j, k in enumerate(keys)})
                         for i in range(every - 1, K, every)]}
+    if args.case == "channel":
+        pa, pb = hist["fp64"][2], hist["mixed"][2]
+        line["mean_u_profile"] = {
+            "averaged_over_steps": K // 4,
+            "max_rel_diff": float(np.abs(pb - pa).max() / np.abs(pa).max()),
+            "y_index_every_8": {"fp64": [float(v) for v in pa[::8]], "mixed": [float(v) for v in pb[::8]]}}
     print(json.dumps(line), flush=True)
     return 0
 
