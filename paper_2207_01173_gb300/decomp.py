@@ -41,8 +41,11 @@ def slab_sizes(nz, world, sizes=None):
 class ZSlabs:
     """This rank's slab of a z-periodic grid and its exchanges."""
 
-    def __init__(self, nz, sizes=None, group=None):
+    def __init__(self, nz, sizes=None, group=None, tagged=True):
+        """tagged=False sends every message with one tag, so that the exchange
+        relies on posting order alone, as it does under NCCL."""
         self.group = group
+        self.tags = (0, 1) if tagged else (0, 0)
         self.world = dist.get_world_size(group) if dist.is_initialized() else 1
         self.rank = dist.get_rank(group) if dist.is_initialized() else 0
         self.sizes = slab_sizes(nz, self.world, sizes)
@@ -70,13 +73,19 @@ class ZSlabs:
             return
         lo = torch.empty_like(bottom)
         hi = torch.empty_like(top)
-        # tag 0 carries bottom planes, tag 1 top planes; with two ranks the
-        # left and right neighbour are the same rank and the tags keep them apart
-        reqs = [dist.isend(bottom, self.left, group=self.group, tag=0),
-                dist.isend(top, self.right, group=self.group, tag=1),
-                dist.irecv(lo, self.left, group=self.group, tag=1),
-                dist.irecv(hi, self.right, group=self.group, tag=0)]
-        for r in reqs:
+        # Every rank sends its bottom planes (tag 0) before its top planes
+        # (tag 1), and receives its high ghosts (the right neighbour's bottom
+        # planes) before its low ghosts (the left neighbour's top planes).
+        # With two ranks the left and right neighbour are the same rank: gloo
+        # tells the two messages apart by tag, NCCL (which ignores tags) by
+        # their order, which this posting order makes agree.  One batch, so
+        # that NCCL never blocks on a send whose receive is not yet posted.
+        tb, tt = self.tags
+        ops = [dist.P2POp(dist.isend, bottom, self.left, group=self.group, tag=tb),
+               dist.P2POp(dist.isend, top, self.right, group=self.group, tag=tt),
+               dist.P2POp(dist.irecv, hi, self.right, group=self.group, tag=tb),
+               dist.P2POp(dist.irecv, lo, self.left, group=self.group, tag=tt)]
+        for r in dist.batch_isend_irecv(ops):
             r.wait()
         q[:, :NG] = lo
         q[:, nk + NG:] = hi

@@ -11,6 +11,10 @@ CASES = {
                    ("tgv", 0.1), 3),
     "tgv_three": ((6, 5, 12), (3, 5, 4), dict(visc=(1, 1.0 / 1600, 1.0 / (1.4 * 0.01), 0.7), Pr=0.72),
                   ("tgv", 0.1), 2),
+    # one tag for every message: the exchange must match by posting order
+    # alone, as under NCCL (two ranks: left and right neighbour coincide)
+    "tgv_untagged": ((6, 5, 8), (4, 4), dict(visc=(1, 1.0 / 1600, 1.0 / (1.4 * 0.01), 0.7), Pr=0.72),
+                     ("tgv", 0.1), 2),
     "channel": ((6, 16, 8), (4, 4), dict(lengths=(2.0, 2.0, 1.0), origin=(0.0, -1.0, 0.0), y_stretch_b=1.5,
                                          visc=(1, 1.0 / 2800, 1.0 / (1.4 * 0.25), 0.7), Pr=0.72,
                                          bc_lo=(0, 1, 0), bc_hi=(0, 1, 0), T_wall=1.0 / (1.4 * 0.25),
@@ -53,7 +57,7 @@ def rank_main(rank, world, port, case, outdir):
     dist.init_process_group("gloo", init_method="tcp://127.0.0.1:%d" % port, rank=rank, world_size=world)
     try:
         n, sizes, kw, _, steps = CASES[case]
-        slabs = ZSlabs(n[2], sizes=sizes if world == len(sizes) else None)
+        slabs = ZSlabs(n[2], sizes=sizes if world == len(sizes) else None, tagged=(case != "tgv_untagged"))
         lengths = kw.get("lengths", (2 * np.pi,) * 3)
         dz = lengths[2] / n[2]
         # the slab's length: nk whole cells of the global size
