@@ -13,17 +13,24 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libhgks_ref.so")
 
 
+def compile_oracle(src, out):
+    """Compile one oracle source file into the shared library `out` (the
+    header is found beside `src` or in this folder)."""
+    tmp = out + ".tmp.%d" % os.getpid()
+    cmd = ["gcc", "-std=c11", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
+           "-fPIC", "-shared", "-I", HERE, "-o", tmp, src, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out
+
+
 def build_oracle(force=False):
     """Build the oracle shared library if missing or stale; return its path."""
     os.makedirs(OUT_DIR, exist_ok=True)
     stale = force or not os.path.exists(LIB) or any(
         os.path.getmtime(p) > os.path.getmtime(LIB) for p in (SRC, HDR))
     if stale:
-        tmp = LIB + ".tmp.%d" % os.getpid()
-        cmd = ["gcc", "-std=c11", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
-               "-fPIC", "-shared", "-o", tmp, SRC, "-lm"]
-        subprocess.run(cmd, check=True)
-        os.replace(tmp, LIB)
+        compile_oracle(SRC, LIB)
     return LIB
 
 

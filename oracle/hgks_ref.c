@@ -190,20 +190,22 @@ static void weno_parts(const double X[5], const weno_point *P, double p[3], doub
 }
 
 /* WENO-Z (Borges et al. 2008, p = 1) value at the point of P, R-W */
-static double weno_z_at(const double X[5], const weno_point *P)
+static double weno_z_eps(const double X[5], const weno_point *P, double eps)
 {
     double p[3], beta[3], alpha[3];
     weno_parts(X, P, p, beta);
     double tau5 = fabs(beta[0] - beta[2]);
     double sa = 0.0;
     for (int k = 0; k < 3; k++) {
-        alpha[k] = P->lin[k] * (1.0 + tau5 / (beta[k] + WENO_EPS));
+        alpha[k] = P->lin[k] * (1.0 + tau5 / (beta[k] + eps));
         sa += alpha[k];
     }
     double v = 0.0;
     for (int k = 0; k < 3; k++) v += (alpha[k] / sa) * p[k];
     return v;
 }
+
+static double weno_z_at(const double X[5], const weno_point *P) { return weno_z_eps(X, P, WENO_EPS); }
 
 static double dot5(const double *w, const double *X)
 {
@@ -857,11 +859,25 @@ static void face_flux_local(const hgks_ref_t h, const double *q, int d, int f, i
     face_flux_one(h, d, f, a, b, dt, rec, Fl, dFl);
 }
 
+/* R-F: a constant body force G is the source S = (0, rho G, rho U.G) in L and
+   its time derivative dS/dt = (0, G L_rho, G.L_rhoU) in dL/dt, where L_rhoU
+   already holds the momentum source */
+static void add_body_force(const hgks_ref_t h, const double *q, size_t p, double Lc[5], double dLc[5])
+{
+    const size_t S = h->ncell_pad;
+    if (h->G[0] == 0.0 && h->G[1] == 0.0 && h->G[2] == 0.0) return;
+    double rho = q[0 * S + p];
+    for (int e = 0; e < 3; e++) Lc[1 + e] += rho * h->G[e];
+    Lc[4] += q[1 * S + p] * h->G[0] + q[2 * S + p] * h->G[1] + q[3 * S + p] * h->G[2];
+    for (int e = 0; e < 3; e++) dLc[1 + e] += h->G[e] * Lc[0];
+    dLc[4] += h->G[0] * Lc[1] + h->G[1] * Lc[2] + h->G[2] * Lc[3];
+}
+
 /* L(Q) and dL/dt(Q) (Eq. "semi2" and its time derivative) of a ghost-filled state */
 static void eval_rhs(const hgks_ref_t h, const double *q, double dt, double *L, double *dL, int record_wall)
 {
     const int nx = h->g.nx, ny = h->g.ny, nz = h->g.nz;
-    const size_t N = h->ncell, S = h->ncell_pad;
+    const size_t N = h->ncell;
     for (int d = 0; d < 3; d++) face_fluxes(h, q, d, dt, h->F[d], h->dF[d]);
     size_t nf[3] = { (size_t)(nx + 1) * ny * nz, (size_t)(ny + 1) * nx * nz, (size_t)(nz + 1) * nx * ny };
     for (int k = 0; k < nz; k++)
@@ -884,16 +900,7 @@ static void eval_rhs(const hgks_ref_t h, const double *q, double dt, double *L, 
                     double tz = h->dF[2][c * nf[2] + fz + 1] - h->dF[2][c * nf[2] + fz];
                     dLc[c] = -((tx + ty) + tz) / vol;
                 }
-                /* R-F: constant body force G as a momentum/energy source */
-                if (h->G[0] != 0.0 || h->G[1] != 0.0 || h->G[2] != 0.0) {
-                    size_t p = pidx(h, i, j, k);
-                    double rho = q[0 * S + p];
-                    double mom[3] = { q[1 * S + p], q[2 * S + p], q[3 * S + p] };
-                    for (int e = 0; e < 3; e++) Lc[1 + e] += rho * h->G[e];
-                    Lc[4] += mom[0] * h->G[0] + mom[1] * h->G[1] + mom[2] * h->G[2];
-                    for (int e = 0; e < 3; e++) dLc[1 + e] += h->G[e] * Lc[0];
-                    dLc[4] += h->G[0] * Lc[1] + h->G[1] * Lc[2] + h->G[2] * Lc[3];
-                }
+                add_body_force(h, q, pidx(h, i, j, k), Lc, dLc);
                 for (int c = 0; c < 5; c++) {
                     L[c * N + ci] = Lc[c];
                     dL[c * N + ci] = dLc[c];
@@ -1203,14 +1210,7 @@ int hgks_ref_rhs_cells(hgks_ref_t h, double dt, int ncells, const int64_t *cells
             Lc[c] = -((sd[0][c] + sd[1][c]) + sd[2][c]) / vol;
             dLc[c] = -((tdd[0][c] + tdd[1][c]) + tdd[2][c]) / vol;
         }
-        if (h->G[0] != 0.0 || h->G[1] != 0.0 || h->G[2] != 0.0) {
-            size_t p = pidx(h, i, j, k), S = h->ncell_pad;
-            double rho = h->q[p];
-            for (int e = 0; e < 3; e++) Lc[1 + e] += rho * h->G[e];
-            Lc[4] += h->q[1 * S + p] * h->G[0] + h->q[2 * S + p] * h->G[1] + h->q[3 * S + p] * h->G[2];
-            for (int e = 0; e < 3; e++) dLc[1 + e] += h->G[e] * Lc[0];
-            dLc[4] += h->G[0] * Lc[1] + h->G[1] * Lc[2] + h->G[2] * Lc[3];
-        }
+        add_body_force(h, h->q, pidx(h, i, j, k), Lc, dLc);
         for (int c = 0; c < 5; c++) { L[(size_t)s * 5 + c] = Lc[c]; dL[(size_t)s * 5 + c] = dLc[c]; }
     }
     return HGKS_REF_OK;
@@ -1430,13 +1430,7 @@ static const weno_point *point_for(double sigma, weno_point *tmp)
 double hgks_ref_weno_z(const double X[5], double sigma, double eps)
 {
     weno_point tmp;
-    const weno_point *P = point_for(sigma, &tmp);
-    double p[3], beta[3], alpha[3];
-    weno_parts(X, P, p, beta);
-    double tau5 = fabs(beta[0] - beta[2]), sa = 0.0, v = 0.0;
-    for (int k = 0; k < 3; k++) { alpha[k] = P->lin[k] * (1.0 + tau5 / (beta[k] + eps)); sa += alpha[k]; }
-    for (int k = 0; k < 3; k++) v += (alpha[k] / sa) * p[k];
-    return v;
+    return weno_z_eps(X, point_for(sigma, &tmp), eps);
 }
 
 void hgks_ref_weno_linear_weights(double sigma, double d[3])

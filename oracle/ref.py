@@ -5,6 +5,7 @@ the two.  Only the test suite, the smoke check and the benchmark's CPU
 baseline may use it.
 """
 import ctypes as C
+import os
 
 import numpy as np
 
@@ -50,9 +51,12 @@ _D = C.POINTER(C.c_double)
 
 
 def lib():
+    """The oracle library: oracle/_build/libhgks_ref.so, or the library named
+    by HGKS_REF_LIB (the pin suite's own check that planted mistakes in a
+    copy of the oracle make its pins fail)."""
     global _lib
     if _lib is None:
-        L = C.CDLL(build_oracle())
+        L = C.CDLL(os.environ.get("HGKS_REF_LIB") or build_oracle())
         L.hgks_ref_create.argtypes = [C.POINTER(Grid), C.c_double, C.c_double, C.POINTER(Visc),
                                       C.POINTER(Bcs), _D, C.POINTER(C.c_void_p)]
         L.hgks_ref_init_tgv.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double]

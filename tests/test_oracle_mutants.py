@@ -1,0 +1,160 @@
+"""Planted mistakes in the oracle must make its pins fail.
+
+Each entry plants one plausible slip (a dropped term, a wrong sign, index or
+coefficient, a swapped operand, a wrong boundary rule) in a copy of
+oracle/hgks_ref.c, builds the copy, and runs the pins named beside it
+against the copy (through HGKS_REF_LIB): at least one of them must fail.
+The original text has to occur exactly once in the oracle, so an edit of the
+oracle that moves or rewrites a planted line shows up here.  Everything runs
+on the CPU; nothing is planted in the CUDA path.
+"""
+import concurrent.futures as cf
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "hgks_ref.c")
+
+K = "tests/test_oracle_kinetic.py::"
+W = "tests/test_oracle_weno.py::"
+S = "tests/test_oracle_solver.py::"
+
+# (name, original text, planted text, pins of which one must fail)
+MUTANTS = [
+    # velocity and internal-energy moments, primitives (Sec. 2)
+    ("half_range_first_moment_sign", "m[1] = U * m[0] + e; }", "m[1] = U * m[0] - e; }",
+     [K + "test_velocity_moments_against_quadrature"]),
+    ("moment_recurrence_index", "(n + 1) / (2.0 * lam) * m[n]", "n / (2.0 * lam) * m[n]",
+     [K + "test_velocity_moments_against_quadrature"]),
+    ("xi4_moment", "K * (K + 2.0) / (4.0 * lam * lam)", "K * K / (4.0 * lam * lam)",
+     [K + "test_internal_moments_against_quadrature"]),
+    ("lambda_factor", "(K + 3.0) * rho / (4.0 * eint)", "(K + 3.0) * rho / (2.0 * eint)",
+     [K + "test_primitive_lambda"]),
+    ("psi4_without_xi", "        p_add(p, 0.5, extra_u, 0, 0, 1);\n", "",
+     [K + "test_micro_slope_against_quadrature"]),
+    ("slope_v_w_transposed", "p_add(p, s * a[2], e[0], e[1] + 1, e[2], e[3]);",
+     "p_add(p, s * a[2], e[0], e[1], e[2] + 1, e[3]);", [K + "test_navier_stokes_limit"]),
+    ("heat_weight_sign", "p_add(p, -1.5 * U0, 2, 0, 0, 0);", "p_add(p, 1.5 * U0, 2, 0, 0, 0);",
+     [K + "test_uniform_state_gives_euler_flux"]),
+    # micro-slopes, compatibility, time integration of the flux (Sec. 2)
+    ("time_slope_sign", "b[i] = -moment2(&pp, &pau, g, R_FULL) / g->rho;",
+     "b[i] = moment2(&pp, &pau, g, R_FULL) / g->rho;", [K + "test_point_flux_against_brute_force"]),
+    ("compat_wrong_half_range", "moment2(&pp, one_poly(), gr, R_NEG);", "moment2(&pp, one_poly(), gr, R_POS);",
+     [K + "test_compat_against_quadrature"]),
+    ("time_coefficient_sign", "- tau * d - tau * d * e;", "- tau * d + tau * d * e;",
+     [K + "test_time_coefficients_against_quadrature"]),
+    ("time_fit_weight", "(4.0 * Ih[i] - If[i]) / dt", "(2.0 * Ih[i] - If[i]) / dt",
+     [K + "test_time_fit_recovers_linear_flux"]),
+    ("nonequilibrium_slope_sign", "- q[4] * B[4][i] - tau", "+ q[4] * B[4][i] - tau",
+     [K + "test_navier_stokes_limit"]),
+    ("equilibrium_time_slope_dropped", "+ q[2] * B[2][i] + q[3]", "+ q[3]",
+     [K + "test_point_flux_against_brute_force"]),
+    ("prandtl_fix_inverted", "(1.0 / gp->Pr - 1.0) * I[5]", "(gp->Pr - 1.0) * I[5]",
+     [K + "test_navier_stokes_limit"]),
+    ("collision_time_mu_over_rho", "viscosity(&gp->visc, T0) / p0", "viscosity(&gp->visc, T0) / W0[0]",
+     [K + "test_point_flux_against_brute_force"]),
+    # WENO-Z and the reconstructions (R-W, R-SL, R-EQ, R-T)
+    ("weno_z_tau_index", "fabs(beta[0] - beta[2])", "fabs(beta[0] - beta[1])",
+     [W + "test_weno_z_avoids_discontinuous_stencil"]),
+    ("weno_z_weight_without_one", "P->lin[k] * (1.0 + tau5 / (beta[k] + eps))",
+     "P->lin[k] * (tau5 / (beta[k] + eps))", [S + "test_free_stream_preserved_bitwise"]),
+    ("smoothness_second_derivative_dropped", "return poly_int_cell(sq1, 3) + poly_int_cell(sq2, 1);",
+     "return poly_int_cell(sq1, 3);", [W + "test_smoothness_indicators_jiang_shu"]),
+    ("normal_slope_edges_swapped", "2.0 * lm_l + 4.0 * lm_r - 6.0 * X[c][2]", "4.0 * lm_l + 2.0 * lm_r - 6.0 * X[c][2]",
+     [S + "test_shear_wave_viscous_decay"]),
+    ("normal_slope_sign", "-4.0 * r_l - 2.0 * r_r + 6.0 * X[c][3]", "4.0 * r_l + 2.0 * r_r - 6.0 * X[c][3]",
+     [S + "test_shear_wave_viscous_decay"]),
+    ("equilibrium_slope_coefficient", "(15.0 * (X[c][3] - X[c][2])", "(16.0 * (X[c][3] - X[c][2])",
+     [S + "test_shear_wave_viscous_decay"]),
+    ("gauss_point_of_wrong_direction", "V[qi][c] = weno_z_at(X, gpt[n]);", "V[qi][c] = weno_z_at(X, gpt[m]);",
+     [S + "test_tgv_reflection_symmetries"]),
+    ("gauss_weight", "Fsum[c] += 0.25 * Fn[c];", "Fsum[c] += 0.5 * Fn[c];", [S + "test_shear_wave_viscous_decay"]),
+    ("tangential_equilibrium_slope_dropped", "dQ0[1][c] = Dt1[2][c] / h1;", "dQ0[1][c] = 0.0;",
+     [S + "test_tgv_swap_symmetry_approximate"]),
+    ("second_tangential_slope_dropped", "dQl[2][c] = Dt2[0][c] / h2;", "dQl[2][c] = 0.0;",
+     [S + "test_tgv_reflection_symmetries"]),
+    ("tangential_cell_size_swapped", "dQ0[2][c] = Dt2[2][c] / h2;", "dQ0[2][c] = Dt2[2][c] / h1;",
+     [S + "test_diagonal_shear_wave_viscous_decay"]),
+    # mesh, boundaries, time step (R-MESH, R-BC, R-DT)
+    ("z_face_area", "else area = dx_(h) * dy_cell(h, ijk[1]);", "else area = dx_(h) * dz_(h);",
+     [S + "test_advection_across_stretched_mesh"]),
+    ("stretch_metric", "return 0.5 * h->g.ly * b * (1.0 - th * th) / tanh(b) * ds;",
+     "return 0.5 * h->g.ly * b * (1.0 - th * th) * ds;", [S + "test_wall_modes_decay"]),
+    ("periodic_ghost_shift", "s = ((g % n) + n) % n;", "s = ((g % n) + n + 1) % n;",
+     [S + "test_conservation_periodic"]),
+    ("wall_slip", "double U = -W[1], V = -W[2], Wv = -W[3];", "double U = W[1], V = -W[2], Wv = -W[3];",
+     [S + "test_channel_wall_shear_laminar"]),
+    ("wall_adiabatic", "double Tg = 2.0 * Tw - T;", "double Tg = T;", [S + "test_wall_modes_decay"]),
+    ("time_step_uniform_y", "double hd[3] = { dx_(h), dy_cell(h, j), dz_(h) };",
+     "double hd[3] = { dx_(h), dx_(h), dz_(h) };", [S + "test_time_step_per_direction"]),
+    ("time_step_normal_velocity", "double v = hd[d] / (fabs(W[1 + d]) + cs);", "double v = hd[d] / (fabs(W[1]) + cs);",
+     [S + "test_time_step_per_direction"]),
+    # S2O4 update and the body force (Eq. "two-stage", R-S2, R-F)
+    ("two_stage_first_coefficient", "+ 0.125 * dt * dt * h->dL1", "+ 0.25 * dt * dt * h->dL1",
+     [S + "test_convergence_order_1d"]),
+    ("two_stage_second_weights", "(h->dL1[c * N + ci] + 2.0 * h->dL2[c * N + ci])",
+     "(2.0 * h->dL1[c * N + ci] + h->dL2[c * N + ci])", [S + "test_convergence_order_1d"]),
+    ("force_time_derivative_momentum_dropped", "for (int e = 0; e < 3; e++) dLc[1 + e] += h->G[e] * Lc[0];", "",
+     [S + "test_body_force_source_and_its_time_derivative"]),
+    ("force_time_derivative_energy_dropped", "dLc[4] += h->G[0] * Lc[1] + h->G[1] * Lc[2] + h->G[2] * Lc[3];", "",
+     [S + "test_body_force_source_and_its_time_derivative"]),
+    ("force_work_dropped", "Lc[4] += q[1 * S + p] * h->G[0] + q[2 * S + p] * h->G[1] + q[3 * S + p] * h->G[2];", "",
+     [S + "test_body_force_source_and_its_time_derivative"]),
+    # diagnostics and initial states (R-STAT, R-INIT, R-NOISE)
+    ("enstrophy_factor", "ens += 0.5 * W[0] * w2 * vol;", "ens += W[0] * w2 * vol;",
+     [S + "test_stats_vorticity_and_dilatation"]),
+    ("dilatation_dropped", "eps += mu * (w2 + 4.0 / 3.0 * div * div) * vol;", "eps += mu * w2 * vol;",
+     [S + "test_stats_vorticity_and_dilatation"]),
+    ("vorticity_sign", "wy = gr[0][2] - gr[2][0]", "wy = gr[0][2] + gr[2][0]",
+     [S + "test_stats_vorticity_and_dilatation"]),
+    ("wall_shear_sign", "s += acc; walls++;", "s -= acc; walls++;", [S + "test_channel_wall_shear_laminar"]),
+    ("tgv_pressure", "(C2x + C2y) * (C2z + 2.0)", "(C2x + C2y) * (C2z + 1.0)",
+     [S + "test_tgv_initial_field_is_exact_cell_average"]),
+    ("channel_profile", "double U = 1.5 * Ub * (1.0 - yn * yn);", "double U = Ub * (1.0 - yn * yn);",
+     [S + "test_channel_wall_shear_laminar"]),
+    ("splitmix_shift", "z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;", "z = (z ^ (z >> 28)) * 0x94D049BB133111EBull;",
+     [S + "test_channel_noise_generator"]),
+    ("density_wave_point_values", "if (kd[d] > 0) fac *= sin(PI * hs[d] / 2.0) / (PI * hs[d] / 2.0);", "",
+     [S + "test_density_wave_initial_field_is_exact_cell_average"]),
+]
+
+
+def _plant_and_run(name, original, planted, pins, workdir):
+    from oracle.build import compile_oracle
+    with open(SRC) as f:
+        src = f.read()
+    if src.count(original) != 1:
+        return "original text occurs %d times" % src.count(original)
+    cpath = os.path.join(workdir, name + ".c")
+    with open(cpath, "w") as f:
+        f.write(src.replace(original, planted))
+    so = compile_oracle(cpath, os.path.join(workdir, name + ".so"))
+    env = dict(os.environ, HGKS_REF_LIB=so, OMP_NUM_THREADS="2")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "--tb=no", "-p", "no:cacheprovider"] + pins,
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    if r.returncode == 1:
+        return None  # a pin failed: the mistake is caught
+    if r.returncode == 0:
+        return "survived: every pin passed"
+    return "pytest exit %d: %s" % (r.returncode, r.stdout[-400:])
+
+
+@pytest.fixture(scope="module")
+def outcomes(tmp_path_factory):
+    workdir = str(tmp_path_factory.mktemp("planted"))
+    workers = max(1, min(8, (os.cpu_count() or 2) // 2))
+    with cf.ThreadPoolExecutor(workers) as ex:
+        futs = {m[0]: ex.submit(_plant_and_run, *m, workdir) for m in MUTANTS}
+        return {k: f.result() for k, f in futs.items()}
+
+
+def test_mutant_names_unique():
+    assert len({m[0] for m in MUTANTS}) == len(MUTANTS)
+
+
+@pytest.mark.parametrize("name", [m[0] for m in MUTANTS])
+def test_pins_catch_planted_mistake(outcomes, name):
+    assert outcomes[name] is None, "%s: %s" % (name, outcomes[name])

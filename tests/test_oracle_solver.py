@@ -291,3 +291,197 @@ def test_sampled_rhs_matches_full_rhs(oracle):
     Lf, dLf = L.reshape(5, -1), dL.reshape(5, -1)
     assert np.array_equal(Ls, Lf[:, cells].T)
     assert np.array_equal(dLs, dLf[:, cells].T)
+
+
+def test_density_wave_initial_field_is_exact_cell_average(oracle):
+    """The density-wave start (the convergence pins' initial state) holds exact
+    cell averages of rho = 1 + a sin(pi (x + y + z)), U = (1, 1, 1), p = 1,
+    checked against 3-D Gauss quadrature on a non-cubic grid."""
+    n, lengths, amp = (6, 5, 4), (2.0, 2.0, 2.0), 0.2
+    s = oracle.RefSolver(n, lengths=lengths)
+    s.init_density_wave(amp)
+    q = s.get_state()
+    hs = [lengths[d] / n[d] for d in range(3)]
+    xg, wg = np.polynomial.legendre.leggauss(8)
+    W = (wg[:, None, None] * wg[None, :, None] * wg[None, None, :]) / 8
+    for (i, j, k) in [(0, 0, 0), (5, 2, 1), (3, 4, 3)]:
+        X, Y, Z = np.meshgrid(*[(c + 0.5 * (xg + 1)) * hs[d] for d, c in enumerate((i, j, k))], indexing="ij")
+        rho = np.sum(W * (1 + amp * np.sin(np.pi * (X + Y + Z))))
+        ref = [rho, rho, rho, rho, 1 / (GAMMA - 1) + 1.5 * rho]
+        np.testing.assert_allclose(q[:, k, j, i], ref, rtol=1e-13)
+
+
+def _accelerated_wave(n, amp, u0, G, p=1.0):
+    """Cell averages and their first two time derivatives, at t = 0, of the
+    exact Euler solution with a constant body force G on [0, 2): rho = 1 + amp
+    sin(pi (x - X(t))), velocity u0 + G t, X' = u_x, uniform p."""
+    h = 2.0 / n
+    xl = np.arange(n) * h
+    xr = xl + h
+    C = (np.cos(np.pi * xl) - np.cos(np.pi * xr)) / (np.pi * h)  # average of sin(pi x)
+    S = (np.sin(np.pi * xr) - np.sin(np.pi * xl)) / h            # average of pi cos(pi x) = d/dx
+    rho, d_rho = 1 + amp * C, -amp * u0[0] * S
+    dd_rho = -amp * (G[0] * S + np.pi ** 2 * u0[0] ** 2 * C)
+    q, dq, ddq = np.zeros((3, 5, n))
+    q[0], dq[0], ddq[0] = rho, d_rho, dd_rho
+    for i in range(3):
+        q[1 + i] = rho * u0[i]
+        dq[1 + i] = u0[i] * d_rho + rho * G[i]
+        ddq[1 + i] = 2 * G[i] * d_rho + u0[i] * dd_rho
+    u2, uG = u0 @ u0, u0 @ G
+    q[4] = p / (GAMMA - 1) + 0.5 * u2 * rho
+    dq[4] = 0.5 * u2 * d_rho + rho * uG
+    ddq[4] = 2 * uG * d_rho + 0.5 * u2 * dd_rho + rho * (G @ G)
+    return q, dq, ddq, S
+
+
+def test_body_force_source_and_its_time_derivative(oracle):
+    """R-F on an exact solution: a density wave carried by a uniform velocity
+    that a constant body force accelerates (inviscid).  L must equal the exact
+    d/dt of the cell averages (fifth order in h).  dL/dt is the time
+    derivative of the interface flux plus dS/dt = (0, G L_rho, G.L_mom); the
+    flux's time slope comes from the force-free compatibility condition, so
+    dL/dt equals the exact second derivative plus the cell average of
+    d/dx[(dF/dQ) S], which for this wave is amp * d(sin)/dx times
+    (G_x, 2 u_x G_x, G_x u_y + u_x G_y, G_x u_z + u_x G_z, (u.G) u_x + |u|^2 G_x / 2)."""
+    amp, u0, G = 0.2, np.array([1.0, 0.3, -0.2]), np.array([0.7, 0.4, 0.5])
+    coef = np.array([G[0], 2 * u0[0] * G[0], G[0] * u0[1] + u0[0] * G[1], G[0] * u0[2] + u0[0] * G[2],
+                     (u0 @ G) * u0[0] + 0.5 * (u0 @ u0) * G[0]])
+    err = {}
+    for n in (32, 64):
+        s = oracle.RefSolver((n, 1, 1), lengths=(2.0, 1.0, 1.0), Pr=1.0, body_force=G)
+        q, dq, ddq, S = _accelerated_wave(n, amp, u0, G)
+        s.set_state(q.reshape(5, 1, 1, n))
+        L, dL = (a.reshape(5, n) for a in s.rhs(1e-3))
+        err[n] = (np.abs(L - dq).max(), np.abs(dL - (ddq + amp * S[None, :] * coef[:, None])).max())
+    assert err[64][0] < 3e-7 and err[32][0] / err[64][0] > 20    # fifth order
+    assert err[64][1] < 5e-6 and err[32][1] / err[64][1] > 10    # fourth order
+
+
+@pytest.mark.parametrize("case", range(3))
+def test_time_step_per_direction(oracle, case):
+    """R-DT on uniform states: dt = CFL min_d h_d / (|u_d| + c), each
+    direction with its own velocity component and cell size (the smallest
+    cell of the tanh-stretched y mesh, Sec. 4.2, in the second case)."""
+    n, lengths, b, vel = [((4, 5, 6), (1.0, 2.0, 3.0), 0.0, (0.2, -1.5, 0.7)),
+                          ((5, 8, 4), (2.0, 2.0, 1.0), 2.0, (0.1, 0.9, -0.4)),
+                          ((6, 6, 6), (1.0, 1.0, 1.0), 0.0, (0.0, 0.0, 2.0))][case]
+    s = oracle.RefSolver(n, lengths=lengths, origin=(0.0, -1.0, 0.0), y_stretch_b=b)
+    rho, p = 1.3, 0.8
+    one = np.ones((n[2], n[1], n[0]))
+    s.set_state(cons(rho * one, vel[0] * one, vel[1] * one, vel[2] * one, p * one))
+    c = np.sqrt(GAMMA * p / rho)
+    if b > 0:
+        sj = 2.0 * np.arange(n[1] + 1) / n[1]
+        dy = np.diff(0.5 * lengths[1] * np.tanh(b * (sj - 1)) / np.tanh(b)).min()
+    else:
+        dy = lengths[1] / n[1]
+    hd = (lengths[0] / n[0], dy, lengths[2] / n[2])
+    assert s.compute_dt(0.4) == pytest.approx(0.4 * min(hd[d] / (abs(vel[d]) + c) for d in range(3)), rel=1e-14)
+
+
+def test_stats_vorticity_and_dilatation(oracle):
+    """R-STAT on a field with known averages (cell-centre point values, N =
+    32, rho = 1): three diagonal shear waves, one per coordinate plane, give
+    |omega|^2 = 6 on average with every vorticity component built from two
+    correlated terms, and compressive waves b sin(x_d) give <(div u)^2> =
+    3 b^2 / 2.  So E_k = 3 (1 + b^2/2) / 2, enstrophy = 3 and eps_com =
+    mu (6 + 2 b^2), the last two within the O(h^4) error of the velocity
+    differences."""
+    N, b, mu, p = 32, 0.3, 0.01, 20.0
+    c = (np.arange(N) + 0.5) * (2 * np.pi / N)
+    z, y, x = np.meshgrid(c, c, c, indexing="ij")
+    u = np.sin(x + z) + np.sin(x + y) + b * np.sin(x)
+    v = -np.sin(x + y) + np.sin(y + z) + b * np.sin(y)
+    w = -np.sin(x + z) - np.sin(y + z) + b * np.sin(z)
+    one = np.ones_like(x)
+    s = oracle.RefSolver((N, N, N), visc=(oracle.VISC_CONSTANT, mu, 1.0, 0.0))
+    s.set_state(cons(one, u, v, w, p * one))
+    st = s.stats()
+    assert st["Ek"] == pytest.approx(1.5 * (1 + b * b / 2), rel=1e-13)
+    assert st["enstrophy"] == pytest.approx(3.0, rel=3e-4)
+    assert st["eps_com"] == pytest.approx(mu * (6 + 2 * b * b), rel=3e-4)
+    assert st["max_mach"] == pytest.approx((np.sqrt(u * u + v * v + w * w) / np.sqrt(GAMMA * p)).max(), rel=1e-14)
+
+
+def _wall_mode_rate(oracle, kind, b, N=32, mu=0.005, Pr=0.72, T=1.0, A=1e-3):
+    s = oracle.RefSolver((1, N, 1), lengths=(1.0, 2.0, 1.0), origin=(0.0, -1.0, 0.0), y_stretch_b=b,
+                         visc=(oracle.VISC_CONSTANT, mu, 1.0, 0.0), Pr=Pr, bc_lo=(0, 1, 0), bc_hi=(0, 1, 0),
+                         T_wall=1.0)
+    sj = 2.0 * np.arange(N + 1) / N
+    yf = np.tanh(b * (sj - 1)) / np.tanh(b) if b > 0 else sj - 1
+    hy = np.diff(yf)
+    k = np.pi
+    sa = (np.cos(k * (yf[:-1] + 1)) - np.cos(k * (yf[1:] + 1))) / (k * hy)  # averages of sin(pi (y + 1))
+    one = np.ones(N)
+    if kind == "shear":
+        q = cons(one, A * sa, 0 * one, 0 * one, one)
+    else:
+        q = cons(1 / (1 + A * sa), 0 * one, 0 * one, 0 * one, one)
+    s.set_state(q.reshape(5, 1, N, 1))
+
+    def amp():
+        qq = s.get_state().reshape(5, N)
+        if kind == "shear":
+            f = qq[1] / qq[0]
+        else:
+            pp = (GAMMA - 1) * (qq[4] - 0.5 * (qq[1] ** 2 + qq[2] ** 2) / qq[0])
+            f = np.log(pp) / GAMMA - np.log(qq[0])
+        return f @ (sa * hy)
+
+    a0 = amp()
+    nst = int(np.ceil(T / s.compute_dt(0.4)))
+    s.step_dt(nst, T / nst)
+    return -np.log(amp() / a0) / T, (mu if kind == "shear" else mu / Pr) * k * k
+
+
+@pytest.mark.parametrize("kind,b", [("shear", 0.0), ("heat", 0.0), ("shear", 2.0), ("heat", 2.0)])
+def test_wall_modes_decay(oracle, kind, b):
+    """R-BC and R-MESH: between isothermal no-slip walls at y = -1, 1 (T_w = 1)
+    the Dirichlet mode sin(pi (y + 1)) of the velocity decays at mu pi^2 / rho
+    and that of the entropy at uniform pressure at mu pi^2 / (rho Pr); the
+    mode has zero mean, so no net heat leaves and the mean pressure stays put.
+    On the uniform mesh within 1.5 %, on the tanh-stretched one (b = 2, the
+    channel's) within 2 %."""
+    rate, exact = _wall_mode_rate(oracle, kind, b)
+    assert rate == pytest.approx(exact, rel=0.015 if b == 0.0 else 0.02)
+
+
+def test_diagonal_shear_wave_viscous_decay(oracle):
+    """A shear wave along the x-z diagonal, u = -w = A sin(x + z), decays at
+    |k|^2 mu / rho = 2 mu / rho: the x-faces see the velocity gradient through
+    their second tangential direction (z) and the z-faces through their first
+    (x).  The single y cell is wider than the x and z cells, so a derivative
+    scaled by the wrong tangential cell size shows."""
+    N, mu, A, T = 20, 0.01, 1e-3, 2.0
+    s = oracle.RefSolver((N, 1, N), lengths=(2 * np.pi, 1.0, 2 * np.pi), visc=(oracle.VISC_CONSTANT, mu, 1.0, 0.0),
+                         Pr=1.0)
+    h = 2 * np.pi / N
+    z, x = np.meshgrid(np.arange(N) * h, np.arange(N) * h, indexing="ij")
+    f = np.sin(x + z + h) * (np.sin(h / 2) / (h / 2)) ** 2  # cell averages of sin(x + z)
+    one = np.ones_like(x)
+    s.set_state(cons(one, A * f, 0 * one, -A * f, one).reshape(5, N, 1, N))
+    s.step_dt(50, T / 50)
+    q = s.get_state().reshape(5, N, N)
+    for comp, sign in ((1, 1.0), (3, -1.0)):
+        amp = sign * (q[comp] * f).sum() / (A * (f * f).sum())
+        assert -np.log(amp) / T == pytest.approx(2 * mu, rel=0.015)
+
+
+def test_advection_across_stretched_mesh(oracle):
+    """A density wave carried along z through the tanh-stretched y mesh
+    (periodic, inviscid) returns after one period: the z-face areas and cell
+    volumes vary with y, and only the right ones keep every y row moving at
+    the same speed."""
+    N, ny = 24, 6
+    s = oracle.RefSolver((1, ny, N), lengths=(1.0, 2.0, 2.0), origin=(0.0, -1.0, 0.0), y_stretch_b=2.0, Pr=1.0)
+    h = 2.0 / N
+    zl = np.arange(N) * h
+    ra = 1 + 0.2 * (np.cos(np.pi * zl) - np.cos(np.pi * (zl + h))) / (np.pi * h)
+    rho = np.broadcast_to(ra[:, None, None], (N, ny, 1))
+    one = np.ones_like(rho)
+    q = cons(rho, 0 * one, 0 * one, one, one)
+    s.set_state(q)
+    nst = int(round(2.0 / (0.2 * h)))
+    s.step_dt(nst, 2.0 / nst)
+    assert np.abs(s.get_state() - q).max() < 1e-4
