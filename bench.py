@@ -169,8 +169,9 @@ def run_reference(args, rank, world):
     rate, el = oracle_rate(args.warmup, args.ref_n)  # warm-up steps (timed region below)
     rate, el = oracle_rate(args.steps, args.ref_n)
     cores = oracle_threads()
-    sample = "TGV %d^3 (same Ma, Re, Pr, viscosity law and CFL; per-cell work equals the %d^3 grid's), " \
-             "%d steps after 1 untimed" % (args.ref_n, args.n, args.steps)
+    sample = "TGV %d^3 (same Ma, Re, Pr, viscosity law and CFL; per-cell work equals the %d^3 grid's): " \
+             "%d warm-up steps on a first solver, then 1 untimed and %d timed steps on a second" \
+             % (args.ref_n, args.n, args.warmup, args.steps)
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": "cell-updates/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
