@@ -8,9 +8,12 @@
 // (fma(a, b, -p) is exact for p = fl(a b)).  The compound operations below
 // follow the usual double-word algorithms built from them; each keeps a
 // relative error of a few units of 2^-46 or better away from underflow.
-// Nothing here may be compiled with fast-math reassociation.
+// Nothing here may be compiled with fast-math reassociation.  The functions
+// are host-callable too, so the same source can be checked on the CPU.
 #pragma once
 #include <cuda_runtime.h>
+
+#define HGKS_FF __host__ __device__ __forceinline__
 
 namespace hgks {
 
@@ -18,7 +21,7 @@ struct ff {
     float hi, lo;
 };
 
-__device__ __forceinline__ ff ff_two_sum(float a, float b)
+HGKS_FF ff ff_two_sum(float a, float b)
 {
     const float s = a + b;
     const float bb = s - a;
@@ -26,26 +29,31 @@ __device__ __forceinline__ ff ff_two_sum(float a, float b)
     return ff{ s, e };
 }
 
-__device__ __forceinline__ ff ff_fast_two_sum(float a, float b)  // needs |a| >= |b| (or a == 0)
+HGKS_FF ff ff_fast_two_sum(float a, float b)  // needs |a| >= |b| (or a == 0)
 {
     const float s = a + b;
     const float e = b - (s - a);
     return ff{ s, e };
 }
 
-__device__ __forceinline__ ff ff_from(float a) { return ff{ a, 0.0f }; }
+HGKS_FF ff ff_from(float a) { return ff{ a, 0.0f }; }
 
 // nearest float-float of an FP64 value (two roundings; exact up to 2^-48 relative)
-__device__ __forceinline__ ff ff_of_double(double x)
+HGKS_FF ff ff_of_double(double x)
 {
+#ifdef __CUDA_ARCH__
     const float h = __double2float_rn(x);
     return ff{ h, __double2float_rn(x - (double)h) };
+#else
+    const float h = (float)x;  // round to nearest, the host's default mode
+    return ff{ h, (float)(x - (double)h) };
+#endif
 }
-__device__ __forceinline__ double ff_to_double(ff a) { return (double)a.hi + (double)a.lo; }
-__device__ __forceinline__ float ff_to_float(ff a) { return a.hi + a.lo; }
+HGKS_FF double ff_to_double(ff a) { return (double)a.hi + (double)a.lo; }
+HGKS_FF float ff_to_float(ff a) { return a.hi + a.lo; }
 
 // x + y, both float-float (accurate even under cancellation)
-__device__ __forceinline__ ff ff_add(ff x, ff y)
+HGKS_FF ff ff_add(ff x, ff y)
 {
     ff s = ff_two_sum(x.hi, y.hi);
     const ff t = ff_two_sum(x.lo, y.lo);
@@ -54,18 +62,18 @@ __device__ __forceinline__ ff ff_add(ff x, ff y)
     s.lo += t.lo;
     return ff_fast_two_sum(s.hi, s.lo);
 }
-__device__ __forceinline__ ff ff_neg(ff x) { return ff{ -x.hi, -x.lo }; }
-__device__ __forceinline__ ff ff_sub(ff x, ff y) { return ff_add(x, ff_neg(y)); }
+HGKS_FF ff ff_neg(ff x) { return ff{ -x.hi, -x.lo }; }
+HGKS_FF ff ff_sub(ff x, ff y) { return ff_add(x, ff_neg(y)); }
 
 // x + b, b a float
-__device__ __forceinline__ ff ff_add_f(ff x, float b)
+HGKS_FF ff ff_add_f(ff x, float b)
 {
     const ff s = ff_two_sum(x.hi, b);
     return ff_fast_two_sum(s.hi, s.lo + x.lo);
 }
 
 // x * y
-__device__ __forceinline__ ff ff_mul(ff x, ff y)
+HGKS_FF ff ff_mul(ff x, ff y)
 {
     const float p = x.hi * y.hi;
     float e = fmaf(x.hi, y.hi, -p);
@@ -74,7 +82,7 @@ __device__ __forceinline__ ff ff_mul(ff x, ff y)
 }
 
 // x * b, b a float
-__device__ __forceinline__ ff ff_mul_f(ff x, float b)
+HGKS_FF ff ff_mul_f(ff x, float b)
 {
     const float p = x.hi * b;
     const float e = fmaf(x.lo, b, fmaf(x.hi, b, -p));
@@ -82,10 +90,10 @@ __device__ __forceinline__ ff ff_mul_f(ff x, float b)
 }
 
 // x * 2^k for an exact power-of-two factor s (no rounding)
-__device__ __forceinline__ ff ff_scale(ff x, float s) { return ff{ x.hi * s, x.lo * s }; }
+HGKS_FF ff ff_scale(ff x, float s) { return ff{ x.hi * s, x.lo * s }; }
 
 // 1 / x: FP32 reciprocal refined by one Newton step on the float-float residual
-__device__ __forceinline__ ff ff_recip(ff x)
+HGKS_FF ff ff_recip(ff x)
 {
     const float r = 1.0f / x.hi;
     float e = fmaf(-x.hi, r, 1.0f);  // exact residual of the leading part
