@@ -98,7 +98,10 @@ static __device__ __forceinline__ void pos_split_mx(const Params &P, const doubl
 }
 
 // stencil deviations x_j = X_j - X_c of float-float values
-static __device__ __forceinline__ float ff_dev(float hj, float lj, float hc, float lc) { return (hj - hc) + (lj - lc); }
+static __host__ __device__ __forceinline__ float ff_dev(float hj, float lj, float hc, float lc)
+{
+    return (hj - hc) + (lj - lc);
+}
 
 // the gas constants of the FP32 flux, held in registers (the batched kernels
 // read Params from global memory, so the point flux takes them by value)
@@ -106,13 +109,13 @@ struct MxGas {
     float gm1, gm1_lo, K, prc, mu_ref, inv_Tref, omega;
     int power_law;
 };
-static __device__ __forceinline__ MxGas mx_gas(const Params &P)
+static __host__ __device__ __forceinline__ MxGas mx_gas(const Params &P)
 {
     return MxGas{ P.f_gm1, P.f_gm1_lo, P.f_K, P.f_prc, P.f_mu_ref, P.f_inv_Tref, P.f_omega, P.visc_kind == 1 };
 }
 
 // FP32 viscosity law
-static __device__ __forceinline__ float viscosity_f(const MxGas &G, float Tm)
+static __host__ __device__ __forceinline__ float viscosity_f(const MxGas &G, float Tm)
 {
     return G.power_law ? G.mu_ref * powf(Tm * G.inv_Tref, G.omega) : G.mu_ref;
 }
@@ -126,9 +129,10 @@ static __device__ __forceinline__ float viscosity_f(const MxGas &G, float Tm)
 // jump is small (trapezoidal form), else Phi(q) itself.  The two sides are
 // done one after the other so that only one side's moment set is live.
 template <bool POS>
-static __device__ __forceinline__ void side_terms_mx(const float q[5], const float dq[3][5], const float jq[5],
-                                                     bool small_jump, float gm1, float K, float b4[5], float w5[5],
-                                                     float b5[5], float w6[5], float b6[5], float cp[5])
+static __host__ __device__ __forceinline__ void side_terms_mx(const float q[5], const float dq[3][5],
+                                                              const float jq[5], bool small_jump, float gm1, float K,
+                                                              float b4[5], float w5[5], float b5[5], float w6[5],
+                                                              float b6[5], float cp[5])
 {
     HalfSide<float> h;
     half_side_setup(q, gm1, K, POS, h);
@@ -169,7 +173,7 @@ static __device__ __forceinline__ void side_terms_mx(const float q[5], const flo
 
 // Q0 = Qm + C from the two sides' compatibility parts: with a small jump
 // C = -(DPhi+(Ql) - DPhi-(Qr))[Qr - Ql] / 2, else Q0 = Phi+(Ql) + Phi-(Qr)
-static __device__ __forceinline__ bool compat_prepare(const ff Ql[5], const ff Qr[5], ff Qm[5], float dq[5])
+static __host__ __device__ __forceinline__ bool compat_prepare(const ff Ql[5], const ff Qr[5], ff Qm[5], float dq[5])
 {
 #pragma unroll
     for (int c = 0; c < 5; c++) {
@@ -178,8 +182,8 @@ static __device__ __forceinline__ bool compat_prepare(const ff Ql[5], const ff Q
     }
     return fabsf(dq[0]) / Qm[0].hi + fabsf(dq[4]) / Qm[4].hi < 1e-3f;
 }
-static __device__ __forceinline__ void compat_finish(bool small_jump, const ff Qm[5], const float cl[5],
-                                                     const float cr[5], ff Q0[5])
+static __host__ __device__ __forceinline__ void compat_finish(bool small_jump, const ff Qm[5], const float cl[5],
+                                                              const float cr[5], ff Q0[5])
 {
 #pragma unroll
     for (int c = 0; c < 5; c++)
@@ -187,7 +191,8 @@ static __device__ __forceinline__ void compat_finish(bool small_jump, const ff Q
 }
 
 // the equilibrium state alone (pass 1): both sides' compatibility parts
-static __device__ __forceinline__ void compat_mixed(const ff Ql[5], const ff Qr[5], float gm1, float K, ff Q0[5])
+static __host__ __device__ __forceinline__ void compat_mixed(const ff Ql[5], const ff Qr[5], float gm1, float K,
+                                                             ff Q0[5])
 {
     ff Qm[5];
     float dq[5], cl[5], cr[5];
@@ -241,8 +246,8 @@ constexpr int FLUX_MX_BLOCK = 128;
 constexpr int FLUX_MX_SMEM = GP_SLOTS * FLUX_MX_BLOCK * (int)sizeof(float);
 
 // the slopes of one state (which = 0: Ql, 1: Qr, 2: Q0) in physical units
-static __device__ __forceinline__ void gp_slopes(const float *col, int st, int n, int which, float ihn, float ih1,
-                                                 float ih2, float dq[3][5])
+static __host__ __device__ __forceinline__ void gp_slopes(const float *col, int st, int n, int which, float ihn,
+                                                          float ih1, float ih2, float dq[3][5])
 {
 #pragma unroll
     for (int c = 0; c < 5; c++) {
@@ -252,8 +257,9 @@ static __device__ __forceinline__ void gp_slopes(const float *col, int st, int n
     }
 }
 
-static __device__ __forceinline__ void gks_point_flux_mixed(const float *col, int st, int n, float ihn, float ih1,
-                                                         float ih2, const MxGas G, float dtf, ff Fn[5], float dFn[5])
+static __host__ __device__ __forceinline__ void gks_point_flux_mixed(const float *col, int st, int n, float ihn,
+                                                                  float ih1, float ih2, const MxGas G, float dtf,
+                                                                  ff Fn[5], float dFn[5])
 {
     const float gm1 = G.gm1, K = G.K;
     ff Ql[5], Qr[5];

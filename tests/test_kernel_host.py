@@ -42,6 +42,9 @@ def kh(tmp_path_factory):
     L.kh_point_flux.argtypes = [C.c_int, dp, dp, dp, dp, dp, C.c_double, C.c_double, C.c_int, C.c_double,
                                 C.c_double, C.c_double, C.c_double, dp, dp]
     L.kh_reconstruct.argtypes = [C.c_int, dp, dp, dp]
+    fp = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
+    L.kh_point_flux_mixed.argtypes = [C.c_int] + [fp] * 7 + [C.c_double, C.c_double, C.c_int, C.c_double,
+                                                              C.c_double, C.c_double, C.c_double, dp, dp]
     return L
 
 
@@ -110,3 +113,42 @@ def test_reconstruction_matches_oracle(oracle, kh, kind):
         ref = [oracle.weno_z(X[i], s) for s in (-0.5, 0.5, -G, G)]
         np.testing.assert_allclose(weno[i], ref, rtol=0, atol=2e-14 * scale)
         np.testing.assert_allclose(quart[i], [Lm @ X[i], Lp @ X[i], Dm @ X[i], Dp @ X[i]], rtol=0, atol=2e-14 * scale)
+
+
+def _split(x):
+    hi = x.astype(np.float32)
+    return hi, (x - hi.astype(np.float64)).astype(np.float32)
+
+
+@pytest.mark.parametrize("jump", [0.0, 1e-4, 1e-3, 0.5, 1.6])
+@pytest.mark.parametrize("visc", sorted(VISC))
+def test_mixed_point_flux_error(oracle, kh, jump, visc):
+    """The mixed-precision Gauss-point flux (R-MX) against the FP64 oracle on
+    the same inputs: float-float states and FP32 slopes, passed to the oracle
+    as the FP64 values they represent.
+
+    Inviscid with a jump below the compatibility switch (1e-3), the flux is
+    the float-float Euler flux of the float-float Q0: within 1e-10 (a
+    float-only B1 would be off by ~1e-7).  Otherwise F^n is within 1e-5 of the
+    flux scale (FP32 small terms, the FP32 direct compatibility sum at larger
+    jumps) and dF^n/dt within 2e-3 of its scale (FP32 throughout, with the
+    cancellation of the time slope of Q0)."""
+    rng = np.random.default_rng([int(round(jump * 1e4)), sorted(VISC).index(visc), 7])
+    n = 150
+    Ql, Qr = _states(rng, n, jump)
+    if jump == 0.0:
+        Qr = Ql.copy()
+    dl, dr, d0 = (np.ascontiguousarray((0.5 * rng.standard_normal((n, 15))).astype(np.float32)) for _ in range(3))
+    (lh, ll), (rh, rl) = _split(Ql), _split(Qr)
+    kind, mu, Tref, om = VISC[visc]
+    dt = 0.01
+    Fn, dFn = np.empty((n, 5)), np.empty((n, 5))
+    kh.kh_point_flux_mixed(n, lh, ll, rh, rl, dl, dr, d0, GAMMA, 0.72, kind, mu, Tref, om, dt, Fn, dFn)
+    ff_only = visc == "inviscid" and jump <= 1e-4
+    for i in range(n):
+        ql, qr = lh[i] + ll[i].astype(np.float64), rh[i] + rl[i].astype(np.float64)
+        _, _, F, dF = oracle.point_flux(ql, qr, dl[i].astype(np.float64), dr[i].astype(np.float64),
+                                        d0[i].astype(np.float64), GAMMA, 0.72, (kind, mu, Tref, om), dt)
+        scale = np.abs(F).max()
+        np.testing.assert_allclose(Fn[i], F, rtol=0, atol=(1e-10 if ff_only else 1e-5) * scale)
+        np.testing.assert_allclose(dFn[i], dF, rtol=0, atol=2e-3 * np.abs(dF).max())
