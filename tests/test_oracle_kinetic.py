@@ -146,6 +146,19 @@ def test_navier_stokes_limit(oracle, Pr):
     assert Fn[4] == pytest.approx(-mu * cp / Pr * s, rel=1e-9)
 
 
+@pytest.mark.parametrize("T", [0.5, 2.0])
+def test_power_law_viscosity_in_shear_stress(oracle, T):
+    """The power law mu = mu_ref (T / T_ref)^omega (Sec. 4.1) enters the
+    collision time: at rest, rho = 1 and temperature T, a normal gradient of
+    tangential momentum gives the shear stress -mu_ref T^omega du_t/dn."""
+    mu_ref, omega, s = 1e-3, 0.7, 0.5
+    Q = _cons(1.0, 0.0, 0.0, 0.0, T)
+    d = np.zeros(15)
+    d[2] = s
+    _, _, Fn, _ = oracle.point_flux(Q, Q, d, d, d, GAMMA, 0.72, (1, mu_ref, 1.0, omega), 1e-2)
+    assert Fn[2] == pytest.approx(-mu_ref * T ** omega * s, rel=1e-9)
+
+
 @pytest.mark.slow
 def test_point_flux_against_brute_force(oracle):
     """Full interface flux with different left/right states and all slopes

@@ -119,6 +119,59 @@ MUTANTS = [
      [S + "test_channel_noise_generator"]),
     ("density_wave_point_values", "if (kd[d] > 0) fac *= sin(PI * hs[d] / 2.0) / (PI * hs[d] / 2.0);", "",
      [S + "test_density_wave_initial_field_is_exact_cell_average"]),
+    # reconstruction tables
+    ("cell_average_of_power", "return (pow(c + 0.5, n + 1) - pow(c - 0.5, n + 1)) / (n + 1);",
+     "return (pow(c + 0.5, n + 1) - pow(c - 0.5, n + 1)) / n;", [W + "test_linear_weights_at_faces"]),
+    ("fit_derivative_power", "else s[n] = (n == 0) ? 0.0 : n * pow(sigma, n - 1);",
+     "else s[n] = (n == 0) ? 0.0 : pow(sigma, n - 1);", [W + "test_quartic_value_and_derivative"]),
+    ("gauss_abscissa", "const double g = sqrt(3.0) / 6.0;", "const double g = sqrt(3.0) / 3.0;",
+     [S + "test_convergence_order_2d_diagonal"]),
+    ("edge_points_swapped", "build_weno_point(&wp[WP_RIGHT], 0.5);", "build_weno_point(&wp[WP_RIGHT], -0.5);",
+     [S + "test_shear_wave_viscous_decay"]),
+    ("tangential_slope_from_value_weights", "Dt1[qi][c] = dot5(gpt[n]->qv, X);", "Dt1[qi][c] = dot5(gpt[n]->qd, X);",
+     [S + "test_tgv_reflection_symmetries"]),
+    # sweep geometry: rotation, tangential order, metrics, areas, volumes
+    ("rotation_of_y_sweep", "{ 0, 2, 1, 3, 4 }", "{ 0, 2, 3, 1, 4 }", [S + "test_tgv_reflection_symmetries"]),
+    ("tangential_order_of_z_sweep", "static const int tdir[3][2] = { { 1, 2 }, { 0, 2 }, { 0, 1 } };",
+     "static const int tdir[3][2] = { { 1, 2 }, { 0, 2 }, { 1, 0 } };", [S + "test_tgv_reflection_symmetries"]),
+    ("normal_metric_at_centre", "double hn = metric(h, d, (double)f);", "double hn = metric(h, d, f + 0.5);",
+     [S + "test_channel_wall_shear_laminar"]),
+    ("x_face_area", "if (d == 0) area = dy_cell(h, ijk[1]) * dz_(h);", "if (d == 0) area = dx_(h) * dz_(h);",
+     [S + "test_body_force_source_and_its_time_derivative"]),
+    ("cell_volume", "double vol = dx_(h) * dy_cell(h, j) * dz_(h);\n                /* face indices",
+     "double vol = dx_(h) * dx_(h) * dz_(h);\n                /* face indices", [S + "test_shear_wave_viscous_decay"]),
+    ("mesh_map_without_normalisation", "return h->g.y0 + 0.5 * h->g.ly * (1.0 + tanh(b * (s - 1.0)) / tanh(b));",
+     "return h->g.y0 + 0.5 * h->g.ly * (1.0 + tanh(b * (s - 1.0)));", [S + "test_time_step_per_direction"]),
+    # ghosts and walls
+    ("ghost_fill_order", "if (e < d) { lo[e] = -NG; hi[e] = n_of(h, e) + NG; }",
+     "if (e > d) { lo[e] = -NG; hi[e] = n_of(h, e) + NG; }", [S + "test_free_stream_preserved_bitwise"]),
+    ("wall_mirror_offset", "else s = side == 0 ? m : n - 1 - m;", "else s = side == 0 ? m + 1 : n - 1 - m;",
+     [S + "test_wall_modes_decay"]),
+    ("wall_ghost_density", "double rho = p / Tg;", "double rho = W[0];", [S + "test_wall_modes_decay"]),
+    ("wall_shear_normalisation", "h->wall_shear = walls ? s / (walls * h->g.lx * h->g.lz) : 0.0;",
+     "h->wall_shear = walls ? s / (walls * h->g.lx) : 0.0;", [S + "test_channel_wall_shear_laminar"]),
+    # S2O4, gas model, kinetic weights
+    ("second_stage_uses_stage_two_rhs", "h->qn[c * S + p] = h->q[c * S + p] + dt * h->L1[c * N + ci]",
+     "h->qn[c * S + p] = h->q[c * S + p] + dt * h->L2[c * N + ci]", [S + "test_advection_across_stretched_mesh"]),
+    ("viscosity_exponent", "return v->mu_ref * pow(T / v->T_ref, v->omega);",
+     "return v->mu_ref * pow(T / v->T_ref, 1.0 - v->omega);", [K + "test_power_law_viscosity_in_shear_stress"]),
+    ("kinetic_energy_factor", "double eint = Q[4] - 0.5 * rho * (U * U + V * V + Wv * Wv);",
+     "double eint = Q[4] - rho * (U * U + V * V + Wv * Wv);", [K + "test_primitive_lambda"]),
+    ("heat_weight_cross_sign", "double cc[3] = { 0.5, -C, 0.5 * C * C };", "double cc[3] = { 0.5, C, 0.5 * C * C };",
+     [K + "test_point_flux_against_brute_force"]),
+    # initial states and diagnostics
+    ("tgv_sin_squared_average", "avs[d][3][i] = 0.5 - 0.5 * avs[d][2][i];", "avs[d][3][i] = 0.5 + 0.5 * avs[d][2][i];",
+     [S + "test_tgv_initial_field_is_exact_cell_average"]),
+    ("noise_scaled_by_bulk_velocity", "U + noise_amp * U * r0", "U + noise_amp * Ub * r0",
+     [S + "test_channel_noise_recipe"]),
+    ("noise_cell_index", "uint64_t idx = ((uint64_t)k * h->g.ny + j) * h->g.nx + i;",
+     "uint64_t idx = ((uint64_t)j * h->g.nz + k) * h->g.nx + i;", [S + "test_channel_noise_recipe"]),
+    ("stats_uniform_y_metric", "double hb = (b == 0) ? dx_(h) : (b == 1 ? dy_dj(h, j + 0.5) : dz_(h));",
+     "double hb = (b == 0) ? dx_(h) : (b == 1 ? dx_(h) : dz_(h));", [S + "test_stats_on_stretched_wall_mesh"]),
+    ("stats_difference_coefficient", "(uu[0][a] - 8.0 * uu[1][a] + 8.0 * uu[2][a] - uu[3][a]) / (12.0 * hb)",
+     "(uu[0][a] - 8.0 * uu[1][a] + 8.0 * uu[2][a] - uu[3][a]) / (6.0 * hb)", [S + "test_stats_vorticity_and_dilatation"]),
+    ("kinetic_energy_not_per_rho0", "o->Ek = ek / (h->rho_ref * vol_tot);", "o->Ek = ek / vol_tot;",
+     [S + "test_diagnostics_normalised_by_rho0"]),
 ]
 
 

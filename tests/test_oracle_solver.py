@@ -485,3 +485,73 @@ def test_advection_across_stretched_mesh(oracle):
     nst = int(round(2.0 / (0.2 * h)))
     s.step_dt(nst, 2.0 / nst)
     assert np.abs(s.get_state() - q).max() < 1e-4
+
+
+def test_diagnostics_normalised_by_rho0(oracle):
+    """R-STAT: E_k and the enstrophy are per unit mass of the reference
+    density rho0, and eps_com = <mu |omega|^2 + ...> / rho0.  The TGV at
+    rho0 = 2 (p0 scales with rho0, so T and mu are unchanged) has the same
+    E_k and enstrophy as at rho0 = 1 and half the eps_com."""
+    r = {}
+    for rho0 in (1.0, 2.0):
+        s = oracle.RefSolver((12, 12, 12), visc=(oracle.VISC_POWER, 1.0 / 1600, 1.0 / (GAMMA * 0.01), 0.7))
+        s.init_tgv(0.1, 1.0, rho0)
+        r[rho0] = s.stats()
+    assert r[2.0]["Ek"] == pytest.approx(r[1.0]["Ek"], rel=1e-13)
+    assert r[2.0]["enstrophy"] == pytest.approx(r[1.0]["enstrophy"], rel=1e-13)
+    assert r[2.0]["eps_com"] == pytest.approx(0.5 * r[1.0]["eps_com"], rel=1e-13)
+
+
+def test_stats_on_stretched_wall_mesh(oracle):
+    """R-STAT on the tanh-stretched channel mesh (b = 2, isothermal walls):
+    u = A sin(pi (y + 1)) at the cell centres gives omega_z = -A pi cos(pi (y + 1)),
+    so the enstrophy is A^2 pi^2 / 4 and eps_com = mu A^2 pi^2 / 2.  The y
+    derivatives must use the local cell size, and the volume weights the
+    stretched cell heights; the midpoint sums are second order."""
+    N, b, A, mu = 32, 2.0, 0.1, 0.01
+    s = oracle.RefSolver((2, N, 2), lengths=(1.0, 2.0, 1.0), origin=(0.0, -1.0, 0.0), y_stretch_b=b,
+                         bc_lo=(0, 1, 0), bc_hi=(0, 1, 0), T_wall=1.0, visc=(oracle.VISC_CONSTANT, mu, 1.0, 0.0))
+    yc = np.tanh(b * (2.0 * (np.arange(N) + 0.5) / N - 1)) / np.tanh(b)
+    u = A * np.sin(np.pi * (yc + 1))
+    one = np.ones((2, N, 2))
+    s.set_state(cons(one, u[None, :, None] * one, 0 * one, 0 * one, one))
+    st = s.stats()
+    assert st["enstrophy"] == pytest.approx(A * A * np.pi ** 2 / 4, rel=3e-3)
+    assert st["eps_com"] == pytest.approx(mu * A * A * np.pi ** 2 / 2, rel=3e-3)
+
+
+def _splitmix64(x):
+    """SplitMix64 (Steele, Lea and Flood, OOPSLA 2014), from its published definition."""
+    m = (1 << 64) - 1
+    z = (x + 0x9E3779B97F4A7C15) & m
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & m
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & m
+    return z ^ (z >> 31)
+
+
+def test_channel_noise_recipe(oracle):
+    """R-NOISE, checked against an independent SplitMix64 (itself checked on the
+    published vectors): cell (i, j, k) with linear index idx = (k ny + j) nx + i
+    draws r_c = (SplitMix64(seed xor (3 idx + c)) >> 11) 2^-52 - 1 for
+    c = 0, 1, 2.  The velocity is u = U(y)(1 + a r0), v = a U_b r1 and
+    w = a U_b r2 (U_b = 1), about the Poiseuille profile U = 1.5 (1 - y^2) at
+    the cell centres of the stretched mesh."""
+    with open(os.path.join(HERE, "golden", "splitmix64.json")) as f:
+        for v in json.load(f)["vectors"]:
+            assert _splitmix64(int(v["x"], 16)) == int(v["out"], 16)
+    nx, ny, nz, seed, a, b = 3, 6, 2, 2800, 0.1, 2.0
+    Tw = 1.0 / (GAMMA * 0.25)
+    s = oracle.RefSolver((nx, ny, nz), lengths=(2 * np.pi, 2.0, np.pi), origin=(0.0, -1.0, 0.0), y_stretch_b=b,
+                         bc_lo=(0, 1, 0), bc_hi=(0, 1, 0), T_wall=Tw)
+    s.init_channel(0.5, a, seed)
+    q = s.get_state()
+    yc = np.tanh(b * (2.0 * (np.arange(ny) + 0.5) / ny - 1)) / np.tanh(b)
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                idx = (k * ny + j) * nx + i
+                r = [(_splitmix64(seed ^ (3 * idx + c)) >> 11) * 2.0 ** -52 - 1 for c in range(3)]
+                U = 1.5 * (1 - yc[j] ** 2)
+                vel = q[1:4, k, j, i] / q[0, k, j, i]
+                np.testing.assert_allclose(vel, [U * (1 + a * r[0]), a * r[1], a * r[2]], rtol=0, atol=1e-15)
+                assert q[0, k, j, i] == 1.0
