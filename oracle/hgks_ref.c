@@ -1216,6 +1216,16 @@ int hgks_ref_rhs_cells(hgks_ref_t h, double dt, int ncells, const int64_t *cells
     return HGKS_REF_OK;
 }
 
+int hgks_ref_face_flux(hgks_ref_t h, double dt, int d, int f, int a, int b, double F[5], double dF[5])
+{
+    if (!h || !F || !dF || d < 0 || d > 2 || !(dt > 0.0)) return HGKS_REF_ERR_INVALID_ARG;
+    if (f < 0 || f > n_of(h, d) || a < 0 || a >= n_of(h, tdir[d][0]) || b < 0 || b >= n_of(h, tdir[d][1]))
+        return HGKS_REF_ERR_INVALID_ARG;
+    ghost_fill(h, h->q);
+    face_flux_local(h, h->q, d, f, a, b, dt, F, dF);
+    return HGKS_REF_OK;
+}
+
 static int state_ok(const hgks_ref_t h, const double *q)
 {
     for (int k = 0; k < h->g.nz; k++)

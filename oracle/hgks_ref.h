@@ -56,6 +56,10 @@ int  hgks_ref_compute_dt(hgks_ref_t h, double cfl, double *dt);
 int  hgks_ref_rhs(hgks_ref_t h, double dt, double *L, double *dL); /* L(Q), dL/dt(Q) of current state */
 /* L, dL/dt at sampled interior cells (index (k ny + j) nx + i); outputs [ncells][5] */
 int  hgks_ref_rhs_cells(hgks_ref_t h, double dt, int ncells, const int64_t *cells, double *L, double *dL);
+/* F^n and dF^n/dt (times the face area, global component order) of the
+   interface of direction d between cells f-1 and f along d, at tangential
+   cell indices (a, b) (Eq. "flux" summed over the 2x2 Gauss points) */
+int  hgks_ref_face_flux(hgks_ref_t h, double dt, int d, int f, int a, int b, double F[5], double dF[5]);
 int  hgks_ref_stats(hgks_ref_t h, hgks_ref_stats_t *out);
 /* Hooks for slab ranks.  halo(user, q) runs after every ghost fill of a
    padded state q ([5][nz+6][ny+6][nx+6]; the physical boundary ghosts are

@@ -71,6 +71,7 @@ def lib():
         L.hgks_ref_rhs.argtypes = [C.c_void_p, C.c_double, _D, _D]
         L.hgks_ref_rhs_cells.argtypes = [C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_int64), _D, _D]
         L.hgks_ref_stats.argtypes = [C.c_void_p, C.POINTER(Stats)]
+        L.hgks_ref_face_flux.argtypes = [C.c_void_p, C.c_double, C.c_int, C.c_int, C.c_int, C.c_int, _D, _D]
         L.hgks_ref_last_error.argtypes = [C.c_void_p]
         L.hgks_ref_last_error.restype = C.c_char_p
         L.hgks_ref_destroy.argtypes = [C.c_void_p]
@@ -221,6 +222,13 @@ class RefSolver:
         self._check(lib().hgks_ref_rhs_cells(self.h, dt, idx.size, idx.ctypes.data_as(C.POINTER(C.c_int64)),
                                              _p(L), _p(dL)), "rhs_cells")
         return L, dL
+
+    def face_flux(self, dt, d, f, a, b):
+        """F^n and dF^n/dt (times the face area) of one interface: direction d,
+        between cells f-1 and f along d, tangential cell indices (a, b)."""
+        F, dF = np.empty(5), np.empty(5)
+        self._check(lib().hgks_ref_face_flux(self.h, dt, d, f, a, b, _p(F), _p(dF)), "face_flux")
+        return F, dF
 
     def stats(self):
         s = Stats()

@@ -136,6 +136,8 @@ MUTANTS = [
      "static const int tdir[3][2] = { { 1, 2 }, { 0, 2 }, { 1, 0 } };", [S + "test_tgv_reflection_symmetries"]),
     ("normal_metric_at_centre", "double hn = metric(h, d, (double)f);", "double hn = metric(h, d, f + 0.5);",
      [S + "test_channel_wall_shear_laminar"]),
+    ("tangential_metric_at_centre", "double h1 = metric(h, tdir[d][0], a + 0.5 + gpt[m]->sigma);",
+     "double h1 = metric(h, tdir[d][0], a + 0.5);", [S + "test_face_stress_uses_metric_at_gauss_points"]),
     ("x_face_area", "if (d == 0) area = dy_cell(h, ijk[1]) * dz_(h);", "if (d == 0) area = dx_(h) * dz_(h);",
      [S + "test_body_force_source_and_its_time_derivative"]),
     ("cell_volume", "double vol = dx_(h) * dy_cell(h, j) * dz_(h);\n                /* face indices",

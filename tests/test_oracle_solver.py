@@ -555,3 +555,41 @@ def test_channel_noise_recipe(oracle):
                 vel = q[1:4, k, j, i] / q[0, k, j, i]
                 np.testing.assert_allclose(vel, [U * (1 + a * r[0]), a * r[1], a * r[2]], rtol=0, atol=1e-15)
                 assert q[0, k, j, i] == 1.0
+
+
+def test_face_stress_uses_metric_at_gauss_points(oracle):
+    """R-MESH on a single interface: reconstruction acts in index space, and a
+    physical derivative is the index derivative divided by dy/dj at the point
+    where it is taken.  Cell averages of a cubic P(eta) over unit index cells
+    are reproduced exactly by the quartics, so on the stretched wall mesh
+    (b = 2) the x-face flux of y-momentum of u = P (at rest otherwise, tiny
+    amplitude) is the Navier-Stokes stress -mu P'(eta)/y'(eta) averaged over
+    the two Gauss points eta = j + 1/2 -+ sqrt3/6, per unit face area.  y' is
+    taken from the map by complex-step differentiation."""
+    N, b, A, mu, nx, nz = 24, 2.0, 1e-3, 0.01, 5, 5
+    s = oracle.RefSolver((nx, N, nz), lengths=(1.0, 2.0, 1.0), origin=(0.0, -1.0, 0.0), y_stretch_b=b,
+                         bc_lo=(0, 1, 0), bc_hi=(0, 1, 0), T_wall=1.0, visc=(oracle.VISC_CONSTANT, mu, 1.0, 0.0),
+                         Pr=1.0)
+
+    def y_of(eta):
+        return np.tanh(b * (2 * eta / N - 1)) / np.tanh(b)
+
+    def dy_deta(eta):
+        return np.imag(y_of(eta + 1e-20j)) / 1e-20
+
+    c = N / 2
+
+    def dP(eta):
+        return 3 * A * (eta - c) ** 2 / c ** 3
+
+    def P_antideriv(eta):
+        return A * c * ((eta - c) / c) ** 4 / 4
+
+    ua = np.array([P_antideriv(j + 1) - P_antideriv(j) for j in range(N)])
+    one = np.ones((nz, N, nx))
+    s.set_state(cons(one, ua[None, :, None] * one, 0 * one, 0 * one, one))
+    g = np.sqrt(3.0) / 6.0
+    rows = range(2, N - 2)  # tangential stencils inside the interior
+    exact = np.array([-mu / 2 * sum(dP(j + 0.5 + sg * g) / dy_deta(j + 0.5 + sg * g) for sg in (-1, 1)) for j in rows])
+    got = np.array([s.face_flux(1e-3, 0, 2, j, 2)[0][2] / ((y_of(j + 1) - y_of(j)) / nz) for j in rows])
+    np.testing.assert_allclose(got, exact, rtol=0, atol=1e-9 * np.abs(exact).max())
