@@ -174,6 +174,52 @@ MUTANTS = [
      "(uu[0][a] - 8.0 * uu[1][a] + 8.0 * uu[2][a] - uu[3][a]) / (6.0 * hb)", [S + "test_stats_vorticity_and_dilatation"]),
     ("kinetic_energy_not_per_rho0", "o->Ek = ek / (h->rho_ref * vol_tot);", "o->Ek = ek / vol_tot;",
      [S + "test_diagnostics_normalised_by_rho0"]),
+    # state transfer, totals, bookkeeping
+    ("set_state_transposed",
+     "h->q[c * h->ncell_pad + pidx(h, i, j, k)] = hq[c * h->ncell + iidx(h, i, j, k)];",
+     "h->q[c * h->ncell_pad + pidx(h, i, j, k)] = hq[c * h->ncell + iidx(h, j % h->g.nx, i % h->g.ny, k)];",
+     [S + "test_shear_wave_viscous_decay"]),
+    ("mass_without_volume", "mass += Q[0] * vol;", "mass += Q[0];", [S + "test_totals_on_stretched_grid"]),
+    ("energy_total_component", "en += Q[4] * vol;", "en += Q[3] * vol;", [S + "test_conservation_periodic"]),
+    ("momentum_total_component", "for (int a = 0; a < 3; a++) mom[a] += Q[1 + a] * vol;",
+     "for (int a = 0; a < 3; a++) mom[a] += Q[1] * vol;", [S + "test_channel_wall_shear_laminar"]),
+    ("max_mach_isothermal_sound", "double cs = sqrt(h->gas.gamma * pr / W[0]);\n                if (sqrt(u2) / cs > mmax)",
+     "double cs = sqrt(pr / W[0]);\n                if (sqrt(u2) / cs > mmax)", [S + "test_stats_vorticity_and_dilatation"]),
+    ("wall_shear_top_wall_dropped", "            s += acc; walls++;\n", "            walls++;\n",
+     [S + "test_channel_wall_shear_laminar"]),
+    ("time_not_advanced", "    h->t += dt;\n", "", [S + "test_time_and_step_bookkeeping"]),
+    # initial states
+    ("tgv_origin_ignored", "if (d == 0) { xl = h->g.x0 + i * dx_(h); xr = xl + dx_(h); }",
+     "if (d == 0) { xl = i * dx_(h); xr = xl + dx_(h); }", [S + "test_tgv_initial_field_with_origin_offset"]),
+    ("tgv_cos_z_average", "double Cz = avs[2][1][k], C2z = avs[2][2][k], ccz = avs[2][4][k];",
+     "double Cz = avs[2][0][k], C2z = avs[2][2][k], ccz = avs[2][4][k];",
+     [S + "test_tgv_initial_field_is_exact_cell_average"]),
+    ("density_wave_velocity_not_momentum", "for (int d = 0; d < 3; d++) h->q[(1 + d) * S + pp] = rho * kd[d];",
+     "for (int d = 0; d < 3; d++) h->q[(1 + d) * S + pp] = kd[d];", [S + "test_density_wave_initial_field_is_exact_cell_average"]),
+    ("channel_wall_temperature", "const double Tw = Ub * Ub / (h->gas.gamma * Ma_b * Ma_b);",
+     "const double Tw = Ub * Ub / (Ma_b * Ma_b);", [S + "test_channel_wall_shear_laminar"]),
+    ("channel_profile_centre", "const double ymid = h->g.y0 + 0.5 * h->g.ly, hh = 0.5 * h->g.ly;",
+     "const double ymid = h->g.y0, hh = 0.5 * h->g.ly;", [S + "test_channel_noise_recipe"]),
+    # time loop
+    ("step_without_ghost_fill",
+     "    for (int s = 0; s < nsteps; s++) {\n        ghost_fill(h, h->q);\n        double m = dt_limit(h, h->q);",
+     "    for (int s = 0; s < nsteps; s++) {\n        double m = dt_limit(h, h->q);", [S + "test_conservation_periodic"]),
+    ("stage_two_without_ghost_fill", "    ghost_fill(h, h->qs);\n    /* stage 2 on Q* */", "    /* stage 2 on Q* */",
+     [S + "test_conservation_periodic"]),
+    # sampled-cell right-hand side (must equal the full one)
+    ("sampled_face_offset", "face_flux_local(h, h->q, d, f + 1, a, b, dt, Fp, dFp);",
+     "face_flux_local(h, h->q, d, f + 1, a, b + (d == 0), dt, Fp, dFp);", [S + "test_sampled_rhs_matches_full_rhs"]),
+    ("sampled_cell_volume", "        double vol = dx_(h) * dy_cell(h, j) * dz_(h);\n        double Lc[5], dLc[5];",
+     "        double vol = dx_(h) * dy_dj(h, j + 0.5) * dz_(h);\n        double Lc[5], dLc[5];",
+     [S + "test_sampled_rhs_matches_full_rhs"]),
+    # kinetic weights and time coefficients
+    ("time_coefficient_q4_decay", "q[4] = 2.0 * tau * tau * (1.0 - e) - tau * d * e;",
+     "q[4] = 2.0 * tau * tau * (1.0 - e) - tau * d;", [K + "test_time_coefficients_against_quadrature"]),
+    ("time_coefficient_q3", "q[3] = tau * (1.0 - e);", "q[3] = tau * e;", [K + "test_time_coefficients_against_quadrature"]),
+    ("heat_weight_without_xi", "p_add(p, 0.5, 1, 0, 0, 1);", "p_add(p, 0.5, 1, 0, 0, 0);",
+     [K + "test_uniform_state_gives_euler_flux"]),
+    ("slope_energy_without_xi", "p_add(p, s * 0.5 * a[4], e[0], e[1], e[2], e[3] + 1);",
+     "p_add(p, s * 0.5 * a[4], e[0], e[1], e[2], e[3]);", [K + "test_navier_stokes_limit"]),
 ]
 
 

@@ -593,3 +593,95 @@ def test_face_stress_uses_metric_at_gauss_points(oracle):
     exact = np.array([-mu / 2 * sum(dP(j + 0.5 + sg * g) / dy_deta(j + 0.5 + sg * g) for sg in (-1, 1)) for j in rows])
     got = np.array([s.face_flux(1e-3, 0, 2, j, 2)[0][2] / ((y_of(j + 1) - y_of(j)) / nz) for j in rows])
     np.testing.assert_allclose(got, exact, rtol=0, atol=1e-9 * np.abs(exact).max())
+
+
+def test_totals_on_stretched_grid(oracle):
+    """R-STAT totals are volume integrals: a uniform state on a non-cubic,
+    tanh-stretched periodic grid has mass rho V, momentum rho u V and energy
+    E V with V = lx ly lz."""
+    n, lengths = (5, 8, 4), (1.5, 2.0, 0.7)
+    rho, vel, p = 1.3, (0.2, -0.1, 0.3), 0.9
+    s = oracle.RefSolver(n, lengths=lengths, origin=(0.0, -1.0, 0.0), y_stretch_b=2.0)
+    one = np.ones((n[2], n[1], n[0]))
+    q = cons(rho * one, vel[0] * one, vel[1] * one, vel[2] * one, p * one)
+    s.set_state(q)
+    st = s.stats()
+    V = np.prod(lengths)
+    assert st["mass"] == pytest.approx(rho * V, rel=1e-14)
+    np.testing.assert_allclose(st["mom"], rho * np.array(vel) * V, rtol=1e-14)
+    assert st["energy"] == pytest.approx(q[4, 0, 0, 0] * V, rel=1e-14)
+
+
+def test_tgv_initial_field_with_origin_offset(oracle):
+    """R-INIT with the box origin moved to (0.3, -0.2, 0.5): the cell averages
+    are those of the Sec. 4.1 fields over the shifted cells (3-D Gauss
+    quadrature)."""
+    n, x0 = 6, (0.3, -0.2, 0.5)
+    s = oracle.RefSolver((n, n, n), origin=x0, visc=(oracle.VISC_POWER, 1.0 / 1600, 1.0 / (GAMMA * 0.01), 0.7))
+    s.init_tgv(0.1, 1.0, 1.0)
+    q = s.get_state()
+    h = 2 * np.pi / n
+    xg, wg = np.polynomial.legendre.leggauss(8)
+    W = (wg[:, None, None] * wg[None, :, None] * wg[None, None, :]) / 8
+    p0 = 1.0 / (GAMMA * 0.01)
+    for (i, j, k) in [(0, 0, 0), (4, 1, 5), (2, 5, 3)]:
+        X, Y, Z = np.meshgrid(*[x0[d] + (c + 0.5 * (xg + 1)) * h for d, c in enumerate((i, j, k))], indexing="ij")
+        u = np.sin(X) * np.cos(Y) * np.cos(Z)
+        v = -np.cos(X) * np.sin(Y) * np.cos(Z)
+        p = p0 + (np.cos(2 * X) + np.cos(2 * Y)) * (np.cos(2 * Z) + 2) / 16
+        ref = [np.sum(W), np.sum(W * u), np.sum(W * v), 0.0, np.sum(W * (p / (GAMMA - 1) + 0.5 * (u * u + v * v)))]
+        np.testing.assert_allclose(q[:, k, j, i], ref, rtol=1e-12, atol=1e-14)
+
+
+def test_time_and_step_bookkeeping(oracle):
+    """hgks_stats reports the time, the step count and the last step's dt:
+    three fixed steps of 0.01, then two CFL steps of a uniform state whose dt
+    is CFL min_d h_d / (|u_d| + c) in closed form."""
+    n, lengths = (6, 5, 4), (1.0, 2.0, 3.0)
+    rho, vel, p = 1.0, (0.3, 0.0, -0.2), 1.0
+    s = oracle.RefSolver(n, lengths=lengths)
+    one = np.ones((n[2], n[1], n[0]))
+    s.set_state(cons(rho * one, vel[0] * one, vel[1] * one, vel[2] * one, p * one))
+    s.step_dt(3, 0.01)
+    st = s.stats()
+    assert st["step"] == 3 and st["t"] == pytest.approx(0.03, rel=1e-15) and st["dt"] == 0.01
+    c = np.sqrt(GAMMA * p / rho)
+    dt = 0.5 * min(lengths[d] / n[d] / (abs(vel[d]) + c) for d in range(3))
+    s.step(2, 0.5)
+    st = s.stats()
+    assert st["step"] == 5
+    assert st["dt"] == pytest.approx(dt, rel=1e-14)
+    assert st["t"] == pytest.approx(0.03 + 2 * dt, rel=1e-14)
+
+
+def test_wall_ghost_definition(oracle):
+    """A definition check of R-BC, not a pin: the ghosts the halo hook sees
+    after a ghost fill are the mirror states U_g = -U, p_g = p,
+    T_g = 2 T_w - T, rho_g = p_g / T_g.  Checked cell by cell against
+    the interior cell each one mirrors, on a state with rho != 1 and flow at
+    the walls.  The physical pins of the walls are the wall-mode decay rates
+    and the laminar wall shear."""
+    n, Tw = (4, 6, 3), 1.1
+    s = oracle.RefSolver(n, lengths=(1.0, 2.0, 1.0), origin=(0.0, -1.0, 0.0), bc_lo=(0, 1, 0), bc_hi=(0, 1, 0),
+                         T_wall=Tw)
+    rng = np.random.default_rng(3)
+    shape = (n[2], n[1], n[0])
+    rho = 1.5 + 0.3 * rng.uniform(-1, 1, shape)
+    vel = 0.4 * rng.uniform(-1, 1, (3,) + shape)
+    p = 1.2 + 0.2 * rng.uniform(-1, 1, shape)
+    s.set_state(cons(rho, *vel, p))
+    seen = []
+    s.set_hooks(halo=lambda q: seen.append(q.copy()))
+    s.stats()  # one ghost fill
+    q = seen[-1]
+    NG = oracle.NG
+    for side in (0, 1):
+        for m in range(NG):
+            jg = NG - 1 - m if side == 0 else NG + n[1] + m          # ghost row (padded index)
+            ji = NG + m if side == 0 else NG + n[1] - 1 - m           # mirrored interior row
+            qi, qg = q[:, NG:-NG, ji, NG:-NG], q[:, NG:-NG, jg, NG:-NG]
+            r, U = qi[0], qi[1:4] / qi[0]
+            pi = (GAMMA - 1) * (qi[4] - 0.5 * r * (U ** 2).sum(0))
+            Tg = 2 * Tw - pi / r
+            rg = pi / Tg
+            np.testing.assert_allclose(qg, cons(rg, *(-U), pi), rtol=1e-13)
