@@ -11,6 +11,7 @@
 #include "../../include/hgks.h"
 #include "hgks_handle.h"
 #include "hgks_kernels.cuh"
+#include "hgks_mesh.h"
 
 #include <algorithm>
 #include <cmath>
@@ -95,46 +96,6 @@ extern "C" size_t hgks_footprint_bytes(const hgks_grid *grid, hgks_precision pre
     size_t doubles = 4 * s.pad + s.fq + s.t1 + s.F[0] + s.F[1] + s.F[2] + 2 * s.cells + s.ytab + s.stats;
     if (precision == HGKS_MIXED) doubles += s.pad;  // the split state
     return doubles * sizeof(double) + sizeof(Ctl);
-}
-
-// ---------------------------------------------------------------------------
-// y metric tables (Sec. 4.2 map; uniform spacing when b = 0)
-// ---------------------------------------------------------------------------
-static double y_at(const hgks_grid &g, double s)  // s = 2 j / ny in [0, 2]
-{
-    if (!(g.y_stretch_b > 0.0)) return g.y0 + 0.5 * s * g.ly;
-    const double b = g.y_stretch_b;
-    return g.y0 + 0.5 * g.ly * (1.0 + std::tanh(b * (s - 1.0)) / std::tanh(b));
-}
-static double dydj_at(const hgks_grid &g, double jpos)
-{
-    const double ds = 2.0 / g.ny;
-    if (!(g.y_stretch_b > 0.0)) return g.ly / g.ny;
-    const double b = g.y_stretch_b, th = std::tanh(b * (jpos * ds - 1.0));
-    return 0.5 * g.ly * b * (1.0 - th * th) / std::tanh(b) * ds;
-}
-
-// layout: my_face[ny+1] | my_gp[2 ny] | my_cen[ny] | hy_cell[ny] | yface[ny+1] | ycen[ny]
-static std::vector<double> y_tables(const hgks_grid &g)
-{
-    const int ny = g.ny;
-    const bool st = g.y_stretch_b > 0.0;
-    std::vector<double> t((size_t)(ny + 1) * 2 + (size_t)ny * 5);
-    double *my_face = t.data(), *my_gp = my_face + ny + 1, *my_cen = my_gp + 2 * ny, *hy = my_cen + ny,
-           *yface = hy + ny, *ycen = yface + ny + 1;
-    const double g6 = std::sqrt(3.0) / 6.0;
-    for (int j = 0; j <= ny; j++) {
-        my_face[j] = dydj_at(g, j);
-        yface[j] = st ? y_at(g, 2.0 * j / ny) : g.y0 + j * (g.ly / ny);
-    }
-    for (int j = 0; j < ny; j++) {
-        my_gp[2 * j] = dydj_at(g, j + 0.5 - g6);
-        my_gp[2 * j + 1] = dydj_at(g, j + 0.5 + g6);
-        my_cen[j] = dydj_at(g, j + 0.5);
-        hy[j] = st ? yface[j + 1] - yface[j] : g.ly / ny;
-        ycen[j] = y_at(g, 2.0 * (j + 0.5) / ny);
-    }
-    return t;
 }
 
 // ---------------------------------------------------------------------------
@@ -245,7 +206,7 @@ extern "C" hgks_status hgks_create(const hgks_grid *grid, double gamma, double P
         delete h;
         return st;
     }
-    std::vector<double> yt = y_tables(*grid);
+    std::vector<double> yt = mesh_y_tables(*grid);
     const int ny = grid->ny;
     P.my_face = h->ytab;
     P.my_gp = h->ytab + ny + 1;

@@ -4,6 +4,7 @@
 // flop model instantiates the same bodies with an operation-counting type.
 #pragma once
 #include "hgks_device.cuh"
+#include "hgks_kernels.cuh"
 
 namespace hgks {
 
@@ -102,6 +103,25 @@ HGKS_HD void tan1_body(Load load, Store store)
 struct FaceGeom {
     double ihn, ih1[2], ih2[2], area;
 };
+
+// the geometry of face f of sweep d (between cells f-1 and f along d) at
+// tangential cell indices (a, b): y metrics from the Params tables (dy/dj at
+// the faces and at the Gauss abscissae), uniform spacings elsewhere; the
+// face area uses the cell height of its y row
+HGKS_HD FaceGeom face_geom(const Params &P, int d, int f, int a, int b)
+{
+    const int e1 = tdir(d, 0), e2 = tdir(d, 1);
+    FaceGeom G;
+    G.ihn = 1.0 / (d == 1 ? P.my_face[f] : P.h[d]);
+    if (d == 0) G.area = P.hy_cell[a] * P.h[2];
+    else if (d == 1) G.area = P.h[0] * P.h[2];
+    else G.area = P.h[0] * P.hy_cell[b];
+    for (int m = 0; m < 2; m++) {
+        G.ih1[m] = 1.0 / (e1 == 1 ? P.my_gp[2 * a + m] : P.h[e1]);
+        G.ih2[m] = 1.0 / (e2 == 1 ? P.my_gp[2 * b + m] : P.h[e2]);
+    }
+    return G;
+}
 
 // second tangential direction, the four Gauss-point fluxes and their sum.
 // load(slot, j): first-pass slot at offset j - 2 along the second tangential

@@ -88,15 +88,7 @@ static __device__ __forceinline__ void pos_flux(const Params &P, int d, const Bo
     const int e1 = tdir(d, 0), e2 = tdir(d, 1);
     const int f = p[d], a = p[e1], b = p[e2];
     const long long base = box_lin(Bt, p), s2 = box_stride(Bt, e2);
-    FaceGeom G;
-    G.ihn = 1.0 / (d == 1 ? P.my_face[f] : P.h[d]);
-    if (d == 0) G.area = P.hy_cell[a] * P.h[2];
-    else if (d == 1) G.area = P.h[0] * P.h[2];
-    else G.area = P.h[0] * P.hy_cell[b];
-    for (int m = 0; m < 2; m++) {
-        G.ih1[m] = 1.0 / (e1 == 1 ? P.my_gp[2 * a + m] : P.h[e1]);
-        G.ih2[m] = 1.0 / (e2 == 1 ? P.my_gp[2 * b + m] : P.h[e2]);
-    }
+    const FaceGeom G = face_geom(P, d, f, a, b);
     auto load = [&](int slot, int j) { return t1[slot * nt + base + (j - 2) * s2]; };
     double Fs[5], dFs[5];
     flux_body<double>(load, G, P, dt, sm + threadIdx.x * FLUX_STRIDE, Fs, dFs);

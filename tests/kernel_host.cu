@@ -2,9 +2,14 @@
 // by case over arrays for tests/test_kernel_host.py: the FP64 templates of
 // paper_2207_01173_gb300/csrc/hgks_device.cuh (the Gauss-point GKS flux,
 // WENO-Z at the cell edges and Gauss points, the quartic value and slope
-// weights) and the mixed-precision Gauss-point flux of hgks_passes_mx.cuh.
+// weights), the mixed-precision Gauss-point flux of hgks_passes_mx.cuh, and
+// the whole FP64 flux of one interface through the three pass bodies of
+// hgks_bodies.cuh with the library's mesh tables and face geometry.
 // Host libm stands in for CUDA's erfc/exp/sqrt/pow here.
+#include "../paper_2207_01173_gb300/csrc/hgks_bodies.cuh"
 #include "../paper_2207_01173_gb300/csrc/hgks_device.cuh"
+#include "../paper_2207_01173_gb300/csrc/hgks_mesh.h"
+#include "../paper_2207_01173_gb300/csrc/hgks_passes.cuh"
 #include "../paper_2207_01173_gb300/csrc/hgks_passes_mx.cuh"
 
 extern "C" {
@@ -89,6 +94,70 @@ void kh_point_flux_mixed(int n, const float *Ql_hi, const float *Ql_lo, const fl
             Fn[5 * i + c] = hgks::ff_to_double(F[c]);
             dFn[5 * i + c] = dF[c];
         }
+    }
+}
+
+// F^n and dF^n/dt (times the face area, global component order) of face f of
+// sweep d at tangential cell indices (a, b), by the FP64 pass bodies: the
+// normal pass on the 5 x 5 tangential neighbourhood, the first tangential
+// pass on its 5 rows, then the flux pass.  q: a ghost-filled padded state
+// [5][nz+6][ny+6][nx+6].
+void kh_face_flux(const double *q, const hgks_grid *grid, double gamma, double Pr, int visc_kind, double mu_ref,
+                  double T_ref, double omega, int d, int f, int a, int b, double dt, double *F, double *dF)
+{
+    using namespace hgks;
+    const std::vector<double> yt = mesh_y_tables(*grid);
+    const int n[3] = { grid->nx, grid->ny, grid->nz };
+    Params P{};
+    for (int e = 0; e < 3; e++) {
+        P.n[e] = n[e];
+        P.np[e] = n[e] + 2 * NG;
+    }
+    P.h[0] = grid->lx / grid->nx;
+    P.h[1] = grid->ly / grid->ny;
+    P.h[2] = grid->lz / grid->nz;
+    P.stretched = grid->y_stretch_b > 0.0;
+    P.my_face = yt.data();
+    P.my_gp = yt.data() + n[1] + 1;
+    P.my_cen = yt.data() + 3 * n[1] + 1;
+    P.hy_cell = yt.data() + 4 * n[1] + 1;
+    P.gamma = gamma;
+    P.K = (5.0 - 3.0 * gamma) / (gamma - 1.0);
+    P.Pr = Pr;
+    P.visc_kind = visc_kind;
+    P.mu_ref = mu_ref;
+    P.T_ref = T_ref;
+    P.omega = omega;
+    const long long cs = (long long)P.np[0] * P.np[1] * P.np[2];
+    auto at = [&](int c, int i, int j, int k) {
+        return q[c * cs + ((long long)(k + NG) * P.np[1] + (j + NG)) * P.np[0] + (i + NG)];
+    };
+    const int e1 = tdir(d, 0), e2 = tdir(d, 1);
+    double rec[5][5][30], t1[5][110];  // rec[t2 offset][t1 offset][slot], t1[t2 offset][slot]
+    for (int jb = 0; jb < 5; jb++)
+        for (int ja = 0; ja < 5; ja++) {
+            auto load = [&](int c, int m) {
+                int ijk[3];
+                ijk[d] = f - 3 + m;
+                ijk[e1] = a - 2 + ja;
+                ijk[e2] = b - 2 + jb;
+                return at(perm_of(d, c), ijk[0], ijk[1], ijk[2]);
+            };
+            auto store = [&](int slot, double v) { rec[jb][ja][slot] = v; };
+            normal_body<double>(load, store, P.K);
+        }
+    for (int jb = 0; jb < 5; jb++) {
+        auto load = [&](int slot, int j) { return rec[jb][j][slot]; };
+        auto store = [&](int slot, double v) { t1[jb][slot] = v; };
+        tan1_body<double>(load, store);
+    }
+    const FaceGeom G = face_geom(P, d, f, a, b);
+    auto load = [&](int slot, int j) { return t1[j][slot]; };
+    double col[110], Fs[5], dFs[5];
+    flux_body<double>(load, G, P, dt, col, Fs, dFs);
+    for (int c = 0; c < 5; c++) {
+        F[perm_of(d, c)] = Fs[c];
+        dF[perm_of(d, c)] = dFs[c];
     }
 }
 
