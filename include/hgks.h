@@ -110,7 +110,11 @@ typedef struct {
  *   grid, visc, bcs: see above (copied).  gamma > 1 (internal degrees of
  *   freedom K = (5 - 3 gamma)/(gamma - 1), Sec. 2).  Pr > 0 (Prandtl number,
  *   applied to the energy flux as F_E += (1/Pr - 1) q).
- *   body_force: constant acceleration (G_x, G_y, G_z) or NULL for none.
+ *   body_force: constant acceleration (G_x, G_y, G_z) or NULL for none.  It
+ *   enters L as the source (0, rho G, rho u.G) and dL/dt as its time
+ *   derivative (0, G L_rho, G.L_mom); the interface flux's time slope comes
+ *   from the force-free compatibility condition, so the forced terms are
+ *   second order in time.
  *   precision: HGKS_FP64 or HGKS_MIXED (see hgks_precision).
  *   cuda_stream: a cudaStream_t, or NULL.
  *   out: receives the handle.
