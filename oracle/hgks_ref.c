@@ -18,6 +18,16 @@
  *
  * Readings of passages the paper leaves open are marked R-xxx; they are the
  * same readings the CUDA path follows (stated independently there).
+ *
+ * Pins: tests/test_oracle_*.py check every part against numerical quadrature,
+ * closed forms, limits, symmetries, convergence orders and the time steps of
+ * the paper's Table 3, and tests/test_oracle_mutants.py plants plausible
+ * slips one at a time, each of which must fail a pin.  Parity unpinned:
+ * agreement with the paper's own implementation, whose code and output the
+ * paper does not print beyond Table 3; and two details that no physical pin
+ * resolves, the rho factor of the wall ghost's kinetic energy (checked only
+ * against the definition of R-BC) and the positivity test of the internal
+ * energy in the bad-state check (a guard that a non-finite value pre-empts).
  */
 #include "hgks_ref.h"
 
