@@ -220,6 +220,58 @@ MUTANTS = [
      [K + "test_uniform_state_gives_euler_flux"]),
     ("slope_energy_without_xi", "p_add(p, s * 0.5 * a[4], e[0], e[1], e[2], e[3] + 1);",
      "p_add(p, s * 0.5 * a[4], e[0], e[1], e[2], e[3]);", [K + "test_navier_stokes_limit"]),
+    # moment engine internals
+    ("maxwellian_v_from_w", "moments_1d(W[2], W[4], R_FULL, 8, g->mu[1]);", "moments_1d(W[3], W[4], R_FULL, 8, g->mu[1]);",
+     [K + "test_micro_slope_against_quadrature"]),
+    ("psi_v_component", "case 2: p_add(p, 1.0, extra_u, 1, 0, 0); break;", "case 2: p_add(p, 1.0, extra_u, 0, 1, 0); break;",
+     [K + "test_micro_slope_against_quadrature"]),
+    ("psi_energy_w_as_v", "        p_add(p, 0.5, extra_u, 0, 2, 0);\n", "        p_add(p, 0.5, extra_u, 2, 0, 0);\n",
+     [K + "test_micro_slope_against_quadrature"]),
+    ("half_ranges_swapped", "const double *mu = (range == R_FULL) ? g->mu[0] : (range == R_POS ? g->mpos : g->mneg);",
+     "const double *mu = (range == R_FULL) ? g->mu[0] : (range == R_POS ? g->mneg : g->mpos);",
+     [K + "test_compat_against_quadrature"]),
+    ("internal_moment_index", "return mu[e[0]] * g->mu[1][e[1]] * g->mu[2][e[2]] * g->mxi[e[3]];",
+     "return mu[e[0]] * g->mu[1][e[1]] * g->mu[2][e[2]] * g->mxi[e[3] > 0 ? e[3] - 1 : 0];",
+     [K + "test_micro_slope_against_quadrature"]),
+    ("slope_rhs_not_per_density", "for (int i = 0; i < 5; i++) b[i] = dQ[i] / g->rho;\n    gauss_solve(5, M, b, a);",
+     "for (int i = 0; i < 5; i++) b[i] = dQ[i];\n    gauss_solve(5, M, b, a);", [K + "test_micro_slope_against_quadrature"]),
+    # point-flux assembly
+    ("equilibrium_term_with_left_slopes", "B[1][i] = moment2(&wgt, &au_0, &g0, R_FULL);",
+     "B[1][i] = moment2(&wgt, &au_l, &g0, R_FULL);", [K + "test_point_flux_against_brute_force"]),
+    ("equilibrium_time_slope_of_left_state", "time_slope_solve(&g0, a0, A0);", "time_slope_solve(&gl, a0, A0);",
+     [K + "test_point_flux_against_brute_force"]),
+    ("right_side_slope_term_range",
+     "B[4][i] = moment2(&wgt, &au_l, &gl, R_POS) + moment2(&wgt, &au_r, &gr, R_NEG);",
+     "B[4][i] = moment2(&wgt, &au_l, &gl, R_POS) + moment2(&wgt, &au_r, &gr, R_POS);",
+     [K + "test_point_flux_against_brute_force"]),
+    ("collision_temperature_of_left_state", "double T0 = 1.0 / (2.0 * W0[4]);", "double T0 = 1.0 / (2.0 * Wl[4]);",
+     [K + "test_point_flux_against_brute_force"]),
+    ("time_fit_slope_factor", "dFn[i] = 4.0 * (If[i] - 2.0 * Ih[i]) / (dt * dt);",
+     "dFn[i] = 2.0 * (If[i] - 2.0 * Ih[i]) / (dt * dt);", [K + "test_time_fit_recovers_linear_flux"]),
+    # sweeps, divergence, diagnostics
+    ("z_metric_from_x", "if (d == 2) return dz_(h);", "if (d == 2) return dx_(h);",
+     [S + "test_advection_across_stretched_mesh"]),
+    ("normal_reconstruction_right_stencil", "const double *sl = &X[c][0], *sr = &X[c][1];",
+     "const double *sl = &X[c][0], *sr = &X[c][0];", [S + "test_shear_wave_viscous_decay"]),
+    ("tangential_values_linear", "T1V[kk][qi][c] = weno_z_at(X, gpt[m]);", "T1V[kk][qi][c] = dot5(gpt[m]->qv, X);",
+     [S + "test_tangential_values_non_oscillatory_at_a_step"]),
+    ("face_records_transposed", "size_t fi = ((size_t)(b + kk) * e1 + (size_t)(a + jj)) * (nd + 1) + f;",
+     "size_t fi = ((size_t)(b + jj) * e1 + (size_t)(a + kk)) * (nd + 1) + f;",
+     [S + "test_diagonal_shear_wave_viscous_decay"]),
+    ("y_face_index_order", "size_t fy = ((size_t)k * nx + i) * (ny + 1) + j;",
+     "size_t fy = ((size_t)i * nz + k) * (ny + 1) + j;", [S + "test_tgv_reflection_symmetries"]),
+    ("z_divergence_sign", "double sz = h->F[2][c * nf[2] + fz + 1] - h->F[2][c * nf[2] + fz];",
+     "double sz = h->F[2][c * nf[2] + fz] - h->F[2][c * nf[2] + fz + 1];",
+     [S + "test_diagonal_shear_wave_viscous_decay"]),
+    ("wall_shear_wrong_row",
+     "for (int i = 0; i < nx; i++) acc += h->F[1][1 * nf[1] + ((size_t)k * nx + i) * (ny + 1) + 0];",
+     "for (int i = 0; i < nx; i++) acc += h->F[1][1 * nf[1] + ((size_t)k * nx + i) * (ny + 1) + 1];",
+     [S + "test_wall_shear_is_the_wall_face_flux"]),
+    ("stats_uniform_cell_volume", "double vol = dx_(h) * dy_cell(h, j) * dz_(h);\n                double Q[5], W[5];",
+     "double vol = dx_(h) * (h->g.ly / h->g.ny) * dz_(h);\n                double Q[5], W[5];",
+     [S + "test_stats_on_stretched_wall_mesh"]),
+    ("noise_w_from_r1", "noise_amp * Ub * r1, noise_amp * Ub * r2, p);", "noise_amp * Ub * r1, noise_amp * Ub * r1, p);",
+     [S + "test_channel_noise_recipe"]),
 ]
 
 

@@ -685,3 +685,42 @@ def test_wall_ghost_definition(oracle):
             Tg = 2 * Tw - pi / r
             rg = pi / Tg
             np.testing.assert_allclose(qg, cons(rg, *(-U), pi), rtol=1e-13)
+
+
+def test_tangential_values_non_oscillatory_at_a_step(oracle):
+    """R-T: the Gauss-point values of the tangential reconstruction come from
+    WENO-Z, so next to a density step across the tangential direction they
+    take the smooth side's value.  On an x-face row the mass flux per unit
+    area then equals u * rho of that row (uniform u and p, inviscid); a
+    linear reconstruction would overshoot by ~1e-3 on the rows next to the
+    step."""
+    nx, ny, u0 = 4, 10, 0.5
+    s = oracle.RefSolver((nx, ny, 1), lengths=(1.0, 1.0, 1.0), Pr=1.0)
+    rho_y = np.where(np.arange(ny) < 5, 1.0, 2.0)  # steps between rows 4|5 and 9|0 (periodic)
+    one = np.ones((1, ny, nx))
+    s.set_state(cons(rho_y[None, :, None] * one, u0 * one, 0 * one, 0 * one, one))
+    area = 1.0 / ny
+    for j in range(ny):
+        F, _ = s.face_flux(1e-3, 0, 2, j, 0)
+        assert F[0] / area == pytest.approx(u0 * rho_y[j], rel=1e-6)
+
+
+def test_wall_shear_is_the_wall_face_flux(oracle):
+    """R-STAT: the reported wall shear is the mean x-momentum flux per unit
+    area through the two wall planes (bottom counted with its outward sign)
+    of the first stage of the last step: it equals the face fluxes of the
+    wall faces, taken one by one, on the state the step started from."""
+    Tw = 1.0 / (GAMMA * 0.25)
+    n, lengths = (5, 10, 4), (2 * np.pi, 2.0, np.pi)
+    s = oracle.RefSolver(n, lengths=lengths, origin=(0.0, -1.0, 0.0), y_stretch_b=2.0,
+                         visc=(oracle.VISC_POWER, 1 / 2800, Tw, 0.7), Pr=0.7, bc_lo=(0, 1, 0), bc_hi=(0, 1, 0),
+                         T_wall=Tw)
+    s.init_channel(0.5, 0.1, 9)
+    q0 = s.get_state()
+    dt = 1e-3
+    s.step_dt(1, dt)
+    ws = s.stats()["wall_shear"]
+    s.set_state(q0)
+    bottom = sum(s.face_flux(dt, 1, 0, i, k)[0][1] for i in range(n[0]) for k in range(n[2]))
+    top = sum(s.face_flux(dt, 1, n[1], i, k)[0][1] for i in range(n[0]) for k in range(n[2]))
+    assert ws == pytest.approx((top - bottom) / (2 * lengths[0] * lengths[2]), rel=1e-12)
