@@ -272,6 +272,40 @@ MUTANTS = [
      [S + "test_stats_on_stretched_wall_mesh"]),
     ("noise_w_from_r1", "noise_amp * Ub * r1, noise_amp * Ub * r2, p);", "noise_amp * Ub * r1, noise_amp * Ub * r1, p);",
      [S + "test_channel_noise_recipe"]),
+    # linear algebra, fitting, smoothness
+    ("pivot_without_rhs_swap", "            double t = b[c]; b[c] = b[p]; b[p] = t;\n", "",
+     [K + "test_micro_slope_against_quadrature"]),
+    ("elimination_factor", "double f = A[r * n + c] / A[c * n + c];", "double f = A[r * n + c] / A[c * n + c] * 0.5;",
+     [K + "test_micro_slope_against_quadrature"]),
+    ("smoothness_first_derivative", "double d1[2] = { c[1], 2.0 * c[2] };", "double d1[2] = { c[1], c[2] };",
+     [W + "test_smoothness_indicators_jiang_shu"]),
+    ("cell_integral_odd_terms", "if (k % 2 == 0) s += c[k] * 2.0 * pow(0.5, k + 1) / (k + 1);",
+     "s += c[k] * 2.0 * pow(0.5, k + 1) / (k + 1);", [W + "test_smoothness_indicators_jiang_shu"]),
+    ("linear_weights_fit_slopes", "for (int j = 0; j < 5; j++) rhs[a] += P->cand[a][j] * P->qv[j];",
+     "for (int j = 0; j < 5; j++) rhs[a] += P->cand[a][j] * P->qd[j];", [W + "test_linear_weights_at_faces"]),
+    # heat-flux weight (Prandtl correction)
+    ("heat_linear_coefficient", "p_add(p, 1.5 * U0 * U0, 1, 0, 0, 0);", "p_add(p, 0.5 * U0 * U0, 1, 0, 0, 0);",
+     [K + "test_uniform_state_gives_euler_flux"]),
+    ("heat_constant_sign", "p_add(p, -0.5 * U0 * U0 * U0, 0, 0, 0, 0);", "p_add(p, 0.5 * U0 * U0 * U0, 0, 0, 0, 0);",
+     [K + "test_uniform_state_gives_euler_flux"]),
+    ("heat_xi_shift_sign", "p_add(p, -0.5 * U0, 0, 0, 0, 1);", "p_add(p, 0.5 * U0, 0, 0, 0, 1);",
+     [K + "test_uniform_state_gives_euler_flux"]),
+    ("heat_cross_shift_sign", "p_add(p, -U0 * cc[q], 0, ev, ew, 0);", "p_add(p, U0 * cc[q], 0, ev, ew, 0);",
+     [K + "test_uniform_state_gives_euler_flux"]),
+    # gas constants, time step, initial states, diagnostics
+    ("internal_degrees_of_freedom", "h->gas.K = (5.0 - 3.0 * gamma) / (gamma - 1.0);",
+     "h->gas.K = (3.0 - gamma) / (gamma - 1.0);", [S + "test_time_step_per_direction"]),
+    ("time_step_isothermal_sound", "double cs = sqrt(h->gas.gamma * pr / W[0]);\n                double hd[3]",
+     "double cs = sqrt(pr / W[0]);\n                double hd[3]", [S + "test_time_step_per_direction"]),
+    ("point_value_energy", "h->q[4 * S + pp] = p / (h->gas.gamma - 1.0) + 0.5 * rho * (u * u + v * v + w * w);",
+     "h->q[4 * S + pp] = p / h->gas.gamma + 0.5 * rho * (u * u + v * v + w * w);", [S + "test_channel_noise_recipe"]),
+    ("tgv_mean_pressure", "const double p0 = rho0 * U0 * U0 / (h->gas.gamma * Ma * Ma);",
+     "const double p0 = rho0 * U0 / (h->gas.gamma * Ma * Ma);", [S + "test_tgv_initial_field_with_origin_offset"]),
+    ("density_wave_energy", "h->q[4 * S + pp] = 1.0 / (h->gas.gamma - 1.0) + 0.5 * rho * (kd[0] + kd[1] + kd[2]);",
+     "h->q[4 * S + pp] = 1.0 / (h->gas.gamma - 1.0) + 0.5 * (kd[0] + kd[1] + kd[2]);",
+     [S + "test_density_wave_initial_field_is_exact_cell_average"]),
+    ("divergence_sign", "double div = gr[0][0] + gr[1][1] + gr[2][2];", "double div = gr[0][0] - gr[1][1] + gr[2][2];",
+     [S + "test_stats_vorticity_and_dilatation"]),
 ]
 
 

@@ -535,7 +535,7 @@ def test_channel_noise_recipe(oracle):
     draws r_c = (SplitMix64(seed xor (3 idx + c)) >> 11) 2^-52 - 1 for
     c = 0, 1, 2.  The velocity is u = U(y)(1 + a r0), v = a U_b r1 and
     w = a U_b r2 (U_b = 1), about the Poiseuille profile U = 1.5 (1 - y^2) at
-    the cell centres of the stretched mesh."""
+    the cell centres of the stretched mesh; rho = 1 and p = T_w = 1/(gamma Ma_b^2)."""
     with open(os.path.join(HERE, "golden", "splitmix64.json")) as f:
         for v in json.load(f)["vectors"]:
             assert _splitmix64(int(v["x"], 16)) == int(v["out"], 16)
@@ -555,6 +555,8 @@ def test_channel_noise_recipe(oracle):
                 vel = q[1:4, k, j, i] / q[0, k, j, i]
                 np.testing.assert_allclose(vel, [U * (1 + a * r[0]), a * r[1], a * r[2]], rtol=0, atol=1e-15)
                 assert q[0, k, j, i] == 1.0
+                p = (GAMMA - 1) * (q[4, k, j, i] - 0.5 * q[0, k, j, i] * (vel ** 2).sum())
+                assert p == pytest.approx(Tw, rel=1e-13)  # rho = 1 at the wall temperature
 
 
 def test_face_stress_uses_metric_at_gauss_points(oracle):
@@ -613,23 +615,24 @@ def test_totals_on_stretched_grid(oracle):
 
 
 def test_tgv_initial_field_with_origin_offset(oracle):
-    """R-INIT with the box origin moved to (0.3, -0.2, 0.5): the cell averages
-    are those of the Sec. 4.1 fields over the shifted cells (3-D Gauss
-    quadrature)."""
-    n, x0 = 6, (0.3, -0.2, 0.5)
+    """R-INIT with the box origin moved to (0.3, -0.2, 0.5), U0 = 2, rho0 = 1.3
+    and Ma = 0.2: the cell averages are those of the Sec. 4.1 fields over the
+    shifted cells, with p0 = rho0 U0^2 / (gamma Ma^2) (3-D Gauss quadrature)."""
+    n, x0, U0, rho0, Ma = 6, (0.3, -0.2, 0.5), 2.0, 1.3, 0.2
     s = oracle.RefSolver((n, n, n), origin=x0, visc=(oracle.VISC_POWER, 1.0 / 1600, 1.0 / (GAMMA * 0.01), 0.7))
-    s.init_tgv(0.1, 1.0, 1.0)
+    s.init_tgv(Ma, U0, rho0)
     q = s.get_state()
     h = 2 * np.pi / n
     xg, wg = np.polynomial.legendre.leggauss(8)
     W = (wg[:, None, None] * wg[None, :, None] * wg[None, None, :]) / 8
-    p0 = 1.0 / (GAMMA * 0.01)
+    p0 = rho0 * U0 ** 2 / (GAMMA * Ma ** 2)
     for (i, j, k) in [(0, 0, 0), (4, 1, 5), (2, 5, 3)]:
         X, Y, Z = np.meshgrid(*[x0[d] + (c + 0.5 * (xg + 1)) * h for d, c in enumerate((i, j, k))], indexing="ij")
-        u = np.sin(X) * np.cos(Y) * np.cos(Z)
-        v = -np.cos(X) * np.sin(Y) * np.cos(Z)
-        p = p0 + (np.cos(2 * X) + np.cos(2 * Y)) * (np.cos(2 * Z) + 2) / 16
-        ref = [np.sum(W), np.sum(W * u), np.sum(W * v), 0.0, np.sum(W * (p / (GAMMA - 1) + 0.5 * (u * u + v * v)))]
+        u = U0 * np.sin(X) * np.cos(Y) * np.cos(Z)
+        v = -U0 * np.cos(X) * np.sin(Y) * np.cos(Z)
+        p = p0 + rho0 * U0 ** 2 * (np.cos(2 * X) + np.cos(2 * Y)) * (np.cos(2 * Z) + 2) / 16
+        E = p / (GAMMA - 1) + 0.5 * rho0 * (u * u + v * v)
+        ref = [rho0 * np.sum(W), rho0 * np.sum(W * u), rho0 * np.sum(W * v), 0.0, np.sum(W * E)]
         np.testing.assert_allclose(q[:, k, j, i], ref, rtol=1e-12, atol=1e-14)
 
 
