@@ -97,6 +97,23 @@ void kh_point_flux_mixed(int n, const float *Ql_hi, const float *Ql_lo, const fl
     }
 }
 
+// equilibrium state Q0 of the mixed path from float-float Ql, Qr (per case
+// 5 hi + 5 lo each); output as hi + lo in FP64
+void kh_compat_mixed(int n, const float *Ql_hi, const float *Ql_lo, const float *Qr_hi, const float *Qr_lo,
+                     double gamma, double *Q0)
+{
+    const float gm1 = (float)(gamma - 1.0), K = (float)((5.0 - 3.0 * gamma) / (gamma - 1.0));
+    for (int i = 0; i < n; i++) {
+        hgks::ff l[5], r[5], q[5];
+        for (int c = 0; c < 5; c++) {
+            l[c] = hgks::ff{ Ql_hi[5 * i + c], Ql_lo[5 * i + c] };
+            r[c] = hgks::ff{ Qr_hi[5 * i + c], Qr_lo[5 * i + c] };
+        }
+        hgks::compat_mixed(l, r, gm1, K, q);
+        for (int c = 0; c < 5; c++) Q0[5 * i + c] = hgks::ff_to_double(q[c]);
+    }
+}
+
 // F^n and dF^n/dt (times the face area, global component order) of face f of
 // sweep d at tangential cell indices (a, b), by the FP64 pass bodies: the
 // normal pass on the 5 x 5 tangential neighbourhood, the first tangential

@@ -47,6 +47,7 @@ def kh(tmp_path_factory):
     fp = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
     L.kh_point_flux_mixed.argtypes = [C.c_int] + [fp] * 7 + [C.c_double, C.c_double, C.c_int, C.c_double,
                                                               C.c_double, C.c_double, C.c_double, dp, dp]
+    L.kh_compat_mixed.argtypes = [C.c_int, fp, fp, fp, fp, C.c_double, dp]
     from oracle import ref
     L.kh_face_flux.argtypes = [dp, C.POINTER(ref.Grid), C.c_double, C.c_double, C.c_int, C.c_double, C.c_double,
                                C.c_double, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, dp, dp]
@@ -203,3 +204,33 @@ def test_face_flux_through_the_pass_bodies(oracle, kh, case):
                     scale = np.abs(F_ref).max()
                     np.testing.assert_allclose(F, F_ref, rtol=0, atol=1e-13 * scale)
                     np.testing.assert_allclose(dF, dF_ref, rtol=0, atol=1e-11 * max(np.abs(dF_ref).max(), scale / dt))
+
+
+def test_mixed_compatibility_error_by_jump(oracle, kh):
+    """R-MX's equilibrium state Q0 against the FP64 compatibility of the
+    oracle, by the relative jump between the l/r states.  Below the 1e-3
+    switch the mixed path forms Qm + C in float-float with the correction C
+    in FP32, so the error is the FP32 rounding of C, about 1e-7 x jump.  The
+    trapezoidal truncation, O(jump^3), lies below that.  Above the switch
+    the direct FP32 sum Phi+(Ql) + Phi-(Qr) keeps FP32 accuracy."""
+    K = (5 - 3 * GAMMA) / (GAMMA - 1)
+    rng = np.random.default_rng(21)
+    n = 60
+    worst = {}
+    for jump in (1e-6, 1e-5, 1e-4, 4e-4, 3e-3, 3e-2):
+        Ql = _cons(rng.uniform(0.8, 1.2, n), *rng.uniform(-0.5, 0.5, (3, n)), rng.uniform(0.8, 1.2, n))
+        # a jump of this relative size in density, velocity and pressure
+        Qr = _cons(Ql[:, 0] * (1 + jump * rng.uniform(-1, 1, n)),
+                   *(Ql[:, 1:4] / Ql[:, :1] + jump * rng.uniform(-1, 1, (n, 3))).T,
+                   (GAMMA - 1) * (Ql[:, 4] - 0.5 * (Ql[:, 1:4] ** 2).sum(1) / Ql[:, 0]) * (1 + jump * rng.uniform(-1, 1, n)))
+        (lh, ll), (rh, rl) = _split(Ql), _split(Qr)
+        Q0 = np.empty((n, 5))
+        kh.kh_compat_mixed(n, lh, ll, rh, rl, GAMMA, Q0)
+        err = 0.0
+        for i in range(n):
+            ref = oracle.compat(lh[i] + ll[i].astype(np.float64), rh[i] + rl[i].astype(np.float64), K)
+            err = max(err, np.abs(Q0[i] - ref).max() / np.abs(ref).max())
+        worst[jump] = err
+    for jump in (1e-6, 1e-5, 1e-4, 4e-4):  # measured: 0.9e-7 x jump
+        assert worst[jump] < 2e-7 * jump + 1e-13, (jump, worst[jump])
+    assert worst[3e-3] < 1e-6 and worst[3e-2] < 1e-6  # direct FP32 sum, measured 1.4e-7
