@@ -26,8 +26,9 @@
  * agreement with the paper's own implementation, whose code and output the
  * paper does not print beyond Table 3; and two details that no physical pin
  * resolves, the rho factor of the wall ghost's kinetic energy (checked only
- * against the definition of R-BC) and the positivity test of the internal
- * energy in the bad-state check (a guard that a non-finite value pre-empts).
+ * against the definition of R-BC) and the positivity tests of density and
+ * internal energy in the bad-state check (guards that a non-finite value
+ * pre-empts).
  */
 #include "hgks_ref.h"
 

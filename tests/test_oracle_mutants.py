@@ -21,6 +21,7 @@ SRC = os.path.join(ROOT, "oracle", "hgks_ref.c")
 K = "tests/test_oracle_kinetic.py::"
 W = "tests/test_oracle_weno.py::"
 S = "tests/test_oracle_solver.py::"
+D = "tests/test_decomp.py::"
 
 # (name, original text, planted text, pins of which one must fail)
 MUTANTS = [
@@ -306,6 +307,29 @@ MUTANTS = [
      [S + "test_density_wave_initial_field_is_exact_cell_average"]),
     ("divergence_sign", "double div = gr[0][0] + gr[1][1] + gr[2][2];", "double div = gr[0][0] - gr[1][1] + gr[2][2];",
      [S + "test_stats_vorticity_and_dilatation"]),
+    # entry points, hooks and the step's bookkeeping
+    ("rhs_without_ghost_fill", "    ghost_fill(h, h->q);\n    eval_rhs(h, h->q, dt, L, dL, 0);",
+     "    eval_rhs(h, h->q, dt, L, dL, 0);", [S + "test_sampled_rhs_matches_full_rhs"]),
+    ("step_ignores_cfl_hook", "        if (h->min_hook) m = h->min_hook(h->hook_user, m);\n        double dt = cfl * m;",
+     "        double dt = cfl * m;", [S + "test_cfl_minimum_hook_applies_to_steps_and_compute_dt"]),
+    ("compute_dt_ignores_cfl_hook",
+     "    double m = dt_limit(h, h->q);\n    if (h->min_hook) m = h->min_hook(h->hook_user, m);\n    *dt = cfl * m;",
+     "    double m = dt_limit(h, h->q);\n    *dt = cfl * m;", [S + "test_cfl_minimum_hook_applies_to_steps_and_compute_dt"]),
+    ("halo_hook_not_called", "    if (h->halo_hook) h->halo_hook(h->hook_user, q);\n", "",
+     [D + "test_split_equals_unsplit"]),
+    ("state_not_swapped", "    double *t = h->q; h->q = h->qn; h->qn = t;\n", "", [S + "test_shear_wave_viscous_decay"]),
+    ("last_dt_not_recorded", "    h->dt_last = dt;\n    return HGKS_REF_OK;", "    return HGKS_REF_OK;",
+     [S + "test_time_and_step_bookkeeping"]),
+    ("first_stage_full_step", "h->qs[c * S + p] = h->q[c * S + p] + 0.5 * dt * h->L1[c * N + ci]",
+     "h->qs[c * S + p] = h->q[c * S + p] + dt * h->L1[c * N + ci]", [S + "test_convergence_order_1d"]),
+    ("wall_shear_from_second_stage", "    eval_rhs(h, h->qs, dt, h->L2, h->dL2, 0);",
+     "    eval_rhs(h, h->qs, dt, h->L2, h->dL2, 1);", [S + "test_wall_shear_is_the_wall_face_flux"]),
+    ("get_state_component_shift",
+     "hq[c * h->ncell + iidx(h, i, j, k)] = h->q[c * h->ncell_pad + pidx(h, i, j, k)];",
+     "hq[c * h->ncell + iidx(h, i, j, k)] = h->q[((c + 1) % 5) * h->ncell_pad + pidx(h, i, j, k)];",
+     [S + "test_free_stream_preserved_bitwise"]),
+    ("stats_density_not_from_tgv", "    h->rho_ref = rho0;\n", "", [S + "test_diagnostics_normalised_by_rho0"]),
+    ("step_counter_increment", "    h->step += 1;\n", "    h->step += 2;\n", [S + "test_time_and_step_bookkeeping"]),
 ]
 
 

@@ -727,3 +727,20 @@ def test_wall_shear_is_the_wall_face_flux(oracle):
     bottom = sum(s.face_flux(dt, 1, 0, i, k)[0][1] for i in range(n[0]) for k in range(n[2]))
     top = sum(s.face_flux(dt, 1, n[1], i, k)[0][1] for i in range(n[0]) for k in range(n[2]))
     assert ws == pytest.approx((top - bottom) / (2 * lengths[0] * lengths[2]), rel=1e-12)
+
+
+def test_cfl_minimum_hook_applies_to_steps_and_compute_dt(oracle):
+    """The slab ranks' CFL hook turns the local minimum of dx/(|u| + c) into
+    the global one.  A hook that halves it must halve both the time step
+    compute_dt reports and the one a CFL step takes (uniform state, so the
+    local minimum is the closed form)."""
+    n, lengths = (5, 4, 6), (1.0, 2.0, 1.5)
+    s = oracle.RefSolver(n, lengths=lengths)
+    one = np.ones((n[2], n[1], n[0]))
+    s.set_state(cons(one, 0.2 * one, 0 * one, 0 * one, one))
+    c = np.sqrt(GAMMA)
+    local = min(lengths[0] / n[0] / (0.2 + c), lengths[1] / n[1] / c, lengths[2] / n[2] / c)
+    s.set_hooks(dtmin=lambda m: 0.5 * m)
+    assert s.compute_dt(0.4) == pytest.approx(0.4 * 0.5 * local, rel=1e-14)
+    s.step(1, 0.4)
+    assert s.stats()["dt"] == pytest.approx(0.4 * 0.5 * local, rel=1e-14)
