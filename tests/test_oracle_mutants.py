@@ -330,6 +330,24 @@ MUTANTS = [
      [S + "test_free_stream_preserved_bitwise"]),
     ("stats_density_not_from_tgv", "    h->rho_ref = rho0;\n", "", [S + "test_diagnostics_normalised_by_rho0"]),
     ("step_counter_increment", "    h->step += 1;\n", "    h->step += 2;\n", [S + "test_time_and_step_bookkeeping"]),
+    # uniform-mesh branches, defaults, small helpers
+    ("uniform_metric_length", "double ds = 2.0 / h->g.ny;\n    if (!stretched(h)) return h->g.ly / h->g.ny;",
+     "double ds = 2.0 / h->g.ny;\n    if (!stretched(h)) return h->g.lz / h->g.ny;", [S + "test_shear_wave_viscous_decay"]),
+    ("uniform_cell_height", "static double dy_cell(const hgks_ref_t h, int j)\n{\n    if (!stretched(h)) return h->g.ly / h->g.ny;",
+     "static double dy_cell(const hgks_ref_t h, int j)\n{\n    if (!stretched(h)) return h->g.lz / h->g.ny;",
+     [S + "test_shear_wave_viscous_decay"]),
+    ("uniform_y_map", "if (!stretched(h)) return h->g.y0 + 0.5 * s * h->g.ly;", "if (!stretched(h)) return h->g.y0 + s * h->g.ly;",
+     [S + "test_channel_noise_recipe"]),
+    ("noise_range_halved", "* (1.0 / 4503599627370496.0) - 1.0;", "* (1.0 / 9007199254740992.0) - 1.0;",
+     [S + "test_channel_noise_recipe"]),
+    ("default_reference_density", "    h->rho_ref = 1.0;\n    h->np[0]", "    h->rho_ref = 2.0;\n    h->np[0]",
+     [S + "test_stats_vorticity_and_dilatation"]),
+    ("density_wave_in_single_cell_directions", "double kd[3] = { h->g.nx > 1, h->g.ny > 1, h->g.nz > 1 };",
+     "double kd[3] = { 1, 1, 1 };", [S + "test_convergence_order_1d"]),
+    ("density_wave_y_spacing", "double hs[3] = { dx_(h), h->g.ly / h->g.ny, dz_(h) };",
+     "double hs[3] = { dx_(h), dx_(h), dz_(h) };", [S + "test_density_wave_initial_field_is_exact_cell_average"]),
+    ("stats_z_spacing", "(b == 1 ? dy_dj(h, j + 0.5) : dz_(h))", "(b == 1 ? dy_dj(h, j + 0.5) : dx_(h))",
+     [S + "test_stats_vorticity_and_dilatation"]),
 ]
 
 
