@@ -361,7 +361,7 @@ def _plant_and_run(name, original, planted, pins, workdir):
     with open(cpath, "w") as f:
         f.write(src.replace(original, planted))
     so = compile_oracle(cpath, os.path.join(workdir, name + ".so"))
-    env = dict(os.environ, HGKS_REF_LIB=so, OMP_NUM_THREADS="2")
+    env = dict(os.environ, HGKS_REF_LIB=so, OMP_NUM_THREADS="1")
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "--tb=no", "-p", "no:cacheprovider"] + pins,
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     if r.returncode == 1:
@@ -374,9 +374,12 @@ def _plant_and_run(name, original, planted, pins, workdir):
 @pytest.fixture(scope="module")
 def outcomes(tmp_path_factory):
     workdir = str(tmp_path_factory.mktemp("planted"))
-    workers = max(1, min(8, (os.cpu_count() or 2) // 2))
+    workers = max(1, min(16, os.cpu_count() or 2))
     with cf.ThreadPoolExecutor(workers) as ex:
-        futs = {m[0]: ex.submit(_plant_and_run, *m, workdir) for m in MUTANTS}
+        # the convergence-order and brute-force pins take longest: start them first
+        slow = ("convergence", "brute_force", "decomp")
+        order = sorted(MUTANTS, key=lambda m: not any(k in p for p in m[3] for k in slow))
+        futs = {m[0]: ex.submit(_plant_and_run, *m, workdir) for m in order}
         return {k: f.result() for k, f in futs.items()}
 
 
