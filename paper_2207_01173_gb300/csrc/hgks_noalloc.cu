@@ -13,12 +13,16 @@
 // dx_d / (|u_d| + c) into its own slot of the array, then one block folds
 // the slots and writes cfl * min to the caller's output.  Every slot that the
 // second pass reads is written by the first pass of the same call, so
-// nothing has to be cleared between calls.
+// nothing has to be cleared between calls.  A cell with a non-positive
+// density or pressure, or a non-finite value, makes its block's slot NaN and
+// the result NaN (fmin alone would drop it and return a finite step).
 #include "../../include/hgks.h"
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdio>
 #include <mutex>
 
 namespace hgks {
@@ -57,6 +61,9 @@ __device__ double na_cell_height(const NaGrid &g, int j)
     return y1 - y0;
 }
 
+// minimum that keeps a NaN (fmin returns the other operand)
+__device__ __forceinline__ double na_min(double a, double b) { return (a != a || b != b) ? NAN : fmin(a, b); }
+
 __global__ void __launch_bounds__(NA_BLOCK) k_na_cfl_partial(NaGrid g, const double *__restrict__ q,
                                                               double *__restrict__ partials)
 {
@@ -70,13 +77,14 @@ __global__ void __launch_bounds__(NA_BLOCK) k_na_cfl_partial(NaGrid g, const dou
         const double p = (g.gamma - 1.0) * (q[4 * g.ncell + t] - 0.5 * rho * (U * U + V * V + W * W));
         const double c = sqrt(g.gamma * p * ir);
         v = fmin(g.hx / (fabs(U) + c), fmin(na_cell_height(g, j) / (fabs(V) + c), g.hz / (fabs(W) + c)));
+        if (!(rho > 0.0) || !(p > 0.0) || !(v < INFINITY)) v = NAN;  // bad cell: no valid step
     }
-    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_down_sync(0xffffffffu, v, o));
+    for (int o = 16; o > 0; o >>= 1) v = na_min(v, __shfl_down_sync(0xffffffffu, v, o));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
     __syncthreads();
     if (threadIdx.x < 32) {
         v = threadIdx.x < NA_BLOCK / 32 ? red[threadIdx.x] : INFINITY;
-        for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_down_sync(0xffffffffu, v, o));
+        for (int o = 16; o > 0; o >>= 1) v = na_min(v, __shfl_down_sync(0xffffffffu, v, o));
         if (threadIdx.x == 0) partials[blockIdx.x] = v;
     }
 }
@@ -86,21 +94,63 @@ __global__ void __launch_bounds__(NA_BLOCK) k_na_cfl_final(const double *__restr
 {
     __shared__ double red[NA_BLOCK / 32];
     double v = INFINITY;
-    for (int b = threadIdx.x; b < nblocks; b += NA_BLOCK) v = fmin(v, partials[b]);
-    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_down_sync(0xffffffffu, v, o));
+    for (int b = threadIdx.x; b < nblocks; b += NA_BLOCK) v = na_min(v, partials[b]);
+    for (int o = 16; o > 0; o >>= 1) v = na_min(v, __shfl_down_sync(0xffffffffu, v, o));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
     __syncthreads();
     if (threadIdx.x < 32) {
         v = threadIdx.x < NA_BLOCK / 32 ? red[threadIdx.x] : INFINITY;
-        for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_down_sync(0xffffffffu, v, o));
+        for (int o = 16; o > 0; o >>= 1) v = na_min(v, __shfl_down_sync(0xffffffffu, v, o));
         if (threadIdx.x == 0) *dt_out = cfl * v;
     }
 }
 
-// device address of g_cfl_partials, looked up once per device with that device current
+// Device address of g_cfl_partials, looked up with the device current, once
+// per device and CUDA context.  The address belongs to the context that
+// loaded this module: after cudaDeviceReset (or when a caller makes another
+// context current) the module is loaded again, possibly at another address,
+// so the cache is keyed by the context's unique id (cuCtxGetId; ids are never
+// reused) and the lookup is repeated when the id changes.  The two driver
+// calls are reached through the runtime's entry-point query, so the library
+// does not link libcuda itself.
 constexpr int NA_MAX_DEVICES = 64;
-static double *g_partials_addr[NA_MAX_DEVICES];
+struct NaSlot {
+    unsigned long long ctx_id;
+    double *addr;
+};
+static NaSlot g_partials_slot[NA_MAX_DEVICES];
 static std::mutex g_setup_mutex;
+
+typedef CUresult (*NaCtxGetCurrent)(CUcontext *);
+typedef CUresult (*NaCtxGetId)(CUcontext, unsigned long long *);
+static NaCtxGetCurrent g_ctx_get_current = nullptr;
+static NaCtxGetId g_ctx_get_id = nullptr;
+
+// id of the context current on this thread (cudaErrorNotSupported if the
+// driver does not offer the two calls; the address is then looked up anew on
+// every call)
+static cudaError_t current_context_id(int dev, unsigned long long *id)
+{
+    *id = 0;
+    if (!g_ctx_get_current || !g_ctx_get_id) {
+        cudaDriverEntryPointQueryResult q1, q2;
+        void *f1 = nullptr, *f2 = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+            q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+            return cudaErrorNotSupported;
+        g_ctx_get_current = (NaCtxGetCurrent)f1;
+        g_ctx_get_id = (NaCtxGetId)f2;
+    }
+    CUcontext ctx = nullptr;
+    if (g_ctx_get_current(&ctx) != CUDA_SUCCESS) return cudaErrorUnknown;
+    if (!ctx) {  // no runtime work on this thread yet: make the device's primary context current
+        cudaError_t e = cudaSetDevice(dev);
+        if (e != cudaSuccess) return e;
+        if (g_ctx_get_current(&ctx) != CUDA_SUCCESS || !ctx) return cudaErrorUnknown;
+    }
+    return g_ctx_get_id(ctx, id) == CUDA_SUCCESS ? cudaSuccess : cudaErrorUnknown;
+}
 
 cudaError_t partials_address(double **out)
 {
@@ -109,13 +159,19 @@ cudaError_t partials_address(double **out)
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= NA_MAX_DEVICES) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_partials_addr[dev]) {
+    unsigned long long id = 0;
+    e = current_context_id(dev, &id);
+    const bool known = e == cudaSuccess;
+    if (!known && e != cudaErrorNotSupported) return e;
+    NaSlot &slot = g_partials_slot[dev];
+    if (!known || !slot.addr || slot.ctx_id != id) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_cfl_partials);
         if (e != cudaSuccess) return e;
-        g_partials_addr[dev] = (double *)p;
+        slot.addr = (double *)p;
+        slot.ctx_id = id;
     }
-    *out = g_partials_addr[dev];
+    *out = slot.addr;
     return cudaSuccess;
 }
 
@@ -139,10 +195,22 @@ extern "C" hgks_status hgks_cfl_dt_noalloc(const hgks_grid *grid, double gamma, 
                                "(33554432) cells, the limit of its fixed scratch");
         return HGKS_ERR_INVALID_ARG;
     }
+    char msg[256];
+    // an error left by earlier, unrelated work: report it as such and leave it pending
+    cudaError_t e = cudaPeekAtLastError();
+    if (e != cudaSuccess) {
+        snprintf(msg, sizeof msg, "hgks_cfl_dt_noalloc: a CUDA error from earlier work is pending: %s",
+                 cudaGetErrorString(e));
+        hgks::set_global_error(msg);
+        return HGKS_ERR_CUDA;
+    }
     double *partials = nullptr;
-    if (partials_address(&partials) != cudaSuccess) {
+    e = partials_address(&partials);
+    if (e != cudaSuccess) {
         cudaGetLastError();
-        hgks::set_global_error("hgks_cfl_dt_noalloc: cudaGetSymbolAddress of the scratch array failed");
+        snprintf(msg, sizeof msg, "hgks_cfl_dt_noalloc: looking up the scratch array's device address failed: %s",
+                 cudaGetErrorString(e));
+        hgks::set_global_error(msg);
         return HGKS_ERR_CUDA;
     }
     NaGrid g;
@@ -159,9 +227,14 @@ extern "C" hgks_status hgks_cfl_dt_noalloc(const hgks_grid *grid, double gamma, 
     const int nblocks = (int)((ncell + NA_BLOCK - 1) / NA_BLOCK);
     cudaStream_t st = (cudaStream_t)cuda_stream;
     k_na_cfl_partial<<<nblocks, NA_BLOCK, 0, st>>>(g, d_q, partials);
-    k_na_cfl_final<<<1, NA_BLOCK, 0, st>>>(partials, nblocks, cfl, d_dt);
-    if (cudaGetLastError() != cudaSuccess) {
-        hgks::set_global_error("hgks_cfl_dt_noalloc: kernel launch failed");
+    e = cudaGetLastError();
+    if (e == cudaSuccess) {
+        k_na_cfl_final<<<1, NA_BLOCK, 0, st>>>(partials, nblocks, cfl, d_dt);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) {
+        snprintf(msg, sizeof msg, "hgks_cfl_dt_noalloc: kernel launch failed: %s", cudaGetErrorString(e));
+        hgks::set_global_error(msg);
         return HGKS_ERR_CUDA;
     }
     return HGKS_OK;
