@@ -54,7 +54,12 @@ typedef enum {
     HGKS_ERR_STATE = 6        /* call not valid in the handle's current state */
 } hgks_status;
 
-typedef enum { HGKS_BC_PERIODIC = 0, HGKS_BC_ISOTHERMAL_WALL = 1 } hgks_bc;
+/* HGKS_BC_EXTERNAL: the three ghost layers of that side belong to a
+ * neighbouring sub-domain and are written by the caller (hgks_halo_set);
+ * the library never fills them.  This is the sub-domain boundary of the
+ * paper's domain decomposition (Sec. 3.2, Alg. 2), accepted in z only (the
+ * slab direction). */
+typedef enum { HGKS_BC_PERIODIC = 0, HGKS_BC_ISOTHERMAL_WALL = 1, HGKS_BC_EXTERNAL = 2 } hgks_bc;
 typedef enum { HGKS_VISC_CONSTANT = 0, HGKS_VISC_POWER = 1 } hgks_visc_kind;
 /* HGKS_FP64: all arithmetic in FP64.  HGKS_MIXED: FP64 for the state and
  * the stage update; reconstruction and flux arithmetic in FP32 on deviations
@@ -86,7 +91,9 @@ typedef struct {
 
 /* Boundary conditions per direction and side (Sec. 4: periodic in every
  * direction for the TGV; periodic x, z and no-slip isothermal walls in y for
- * the channel).  Walls need at least 3 cells in their direction. */
+ * the channel).  Walls need at least 3 cells in their direction, and so do
+ * EXTERNAL sides (a neighbour's ghost layers come from this sub-domain's
+ * three boundary layers alone). */
 typedef struct {
     hgks_bc lo[3], hi[3];
     double T_wall;
@@ -201,6 +208,69 @@ typedef struct {
  * precision other than FP64). */
 hgks_status hgks_flop_model(const hgks_grid *grid, hgks_precision precision, hgks_flop_model_t *out);
 
+/* ---- sub-domains: one step taken in phases -----------------------------
+ * The paper splits the grid over GPUs and, before each stage of a step,
+ * exchanges the ghost layers of neighbouring sub-domains and takes the
+ * global minimum of the CFL limit (Sec. 3.2, Alg. 2 and the MPI+CUDA
+ * communication figure).  A handle whose z sides are HGKS_BC_EXTERNAL is one
+ * such sub-domain (a slab of whole z planes), and one step of the whole
+ * domain runs as
+ *     dt = min over sub-domains of hgks_compute_dt(h, cfl)     (global CFL)
+ *     for stage s = 1, 2 (state 0 = the current state, 1 = the stage state):
+ *         hgks_fill_ghosts(h, s - 1)       on every sub-domain
+ *         hgks_halo_get(h, s - 1, 2, side, buf) on every sub-domain and side
+ *         hgks_halo_set(h', s - 1, 2, other side, buf) on its neighbour h'
+ *         hgks_stage(h, s, dt)             on every sub-domain
+ * which gives, cell for cell, the same numbers as hgks_step on the whole
+ * grid.  The diagnostics of a sub-domain (hgks_stats) are volume averages over
+ * that sub-domain; set the halos of the current state first, since the
+ * vorticity stencils reach into them.  Buffers are device memory owned by the caller; nothing is allocated
+ * by these calls.  All work is enqueued on the handle's stream; to hand a
+ * buffer from one handle to another on a different stream, order the two
+ * streams (an event) or use one stream. */
+enum { HGKS_STATE_CURRENT = 0, HGKS_STATE_STAGE = 1 };
+
+/* Fill the ghost layers of a state (HGKS_STATE_CURRENT: the current state
+ * Q^n; HGKS_STATE_STAGE: the stage state Q* of the step in progress) on every
+ * side that is not EXTERNAL: periodic copies, wall mirrors, in the order x,
+ * y, z as hgks_step does, so edge and corner ghosts are filled too.
+ * Errors: INVALID_ARG (NULL handle, bad state index). */
+hgks_status hgks_fill_ghosts(hgks_t h, int state);
+
+/* Doubles in one halo buffer of direction dir (only dir = 2, z, is
+ * supported): 5 components x 3 layers x (ny + 6) x (nx + 6), i.e. whole
+ * padded planes with their x and y ghosts.  0 for an invalid argument. */
+size_t hgks_halo_count(hgks_t h, int dir);
+
+/* Copy the three boundary layers next to side (0: low, 1: high) of direction
+ * dir (2) of a state, with the x and y ghost cells of each plane, into d_buf
+ * (device pointer, hgks_halo_count(h, dir) doubles, layout
+ * [5][3][ny + 6][nx + 6], layers ordered by increasing z).  Fill the x / y
+ * ghosts (hgks_fill_ghosts) first: they travel with the planes, which makes
+ * the stencil corners right.  Asynchronous on the handle's stream.
+ * Errors: INVALID_ARG (NULL, dir != 2, side or state out of range). */
+hgks_status hgks_halo_get(hgks_t h, int state, int dir, int side, double *d_buf);
+
+/* Write d_buf (device pointer, layout as for hgks_halo_get) into the three
+ * ghost layers on side (0: low, 1: high) of direction dir (2) of a state.
+ * For a slab decomposition the low ghosts of a slab are the high boundary
+ * layers of its lower neighbour, and the other way round.  Asynchronous on
+ * the handle's stream.
+ * Errors: INVALID_ARG (NULL, dir != 2, side or state out of range). */
+hgks_status hgks_halo_set(hgks_t h, int state, int dir, int side, const double *d_buf);
+
+/* One stage of the step with time step dt > 0 (Eq. "two-stage"), on a state
+ * whose ghost layers are all set (hgks_fill_ghosts plus the halos):
+ *   stage 1: the three sweeps on Q^n, then Q* = Q^n + dt/2 L + dt^2/8 dL and
+ *            R = Q^n + dt L + dt^2/6 dL;
+ *   stage 2: the three sweeps on Q*, then Q^{n+1} = R + dt^2/3 dL(Q*), and
+ *            the step is committed (t += dt, step + 1).
+ * Stage 2 reads the device status once (as hgks_step does) and reports a bad
+ * state with NONFINITE, leaving the state at the last completed step.
+ * Errors: INVALID_ARG (stage not 1 or 2, dt <= 0), STATE (stage 2 without a
+ * stage 1 of the same step), NONFINITE, CUDA. */
+hgks_status hgks_stage(hgks_t h, int stage, double dt);
+
 /* Largest grid (cells) accepted by hgks_cfl_dt_noalloc. */
 #define HGKS_NOALLOC_MAX_CELLS 33554432
 
@@ -231,8 +301,19 @@ hgks_status hgks_flop_model(const hgks_grid *grid, hgks_precision precision, hgk
  * whose work overlaps on the GPU race with each other: serialise them on one
  * stream.  The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture begins.
- * Errors: INVALID_ARG (NULL pointer, bad sizes, too many cells), CUDA. */
+ * before any stream capture begins.  The address is kept per CUDA context:
+ * after cudaDeviceReset, or under another current context, the next call
+ * looks it up again (so that call, too, should come before a capture).
+ * Invalid state: if any cell has a non-positive density or pressure, or a
+ * non-finite value, *d_dt receives NaN (no cell is silently skipped).
+ * Wall-stretched grids (y_stretch_b > 0): the cell heights are computed on
+ * the device with the device tanh, while hgks_compute_dt takes them from a
+ * host table, so on such grids the two agree to about 1e-13 relative (the
+ * rounding of a difference of two tanh values), not bit for bit; on uniform
+ * grids they agree to the last bit.
+ * Errors: INVALID_ARG (NULL pointer, bad sizes, too many cells), CUDA (a
+ * launch failed, or a CUDA error from earlier work was already pending: it is
+ * reported with its own text and left pending). */
 hgks_status hgks_cfl_dt_noalloc(const hgks_grid *grid, double gamma, double cfl, const double *d_q,
                                 double *d_dt, void *cuda_stream);
 
@@ -266,7 +347,8 @@ typedef struct {
 } hgks_batch_info_t;
 /* handles: n distinct handles on one stream (n >= 1).  *out receives the
  * batch.  Errors: INVALID_ARG (NULL, n < 1, a repeated handle, handles on
- * different streams), CUDA (allocation of the work-lists). */
+ * different streams, a handle with EXTERNAL sides), CUDA (allocation of the
+ * work-lists). */
 hgks_status hgks_batch_create(hgks_t *handles, int n, hgks_batch_t *out);
 /* nsteps (>= 0) steps of every problem, each with its own CFL time step
  * cfl * min over cells of dx_d / (|u_d| + c).  Work queued earlier on the

@@ -135,10 +135,17 @@ extern "C" hgks_status hgks_create(const hgks_grid *grid, double gamma, double P
     const int n[3] = { grid->nx, grid->ny, grid->nz };
     for (int d = 0; d < 3; d++) {
         bool wall = bcs->lo[d] == HGKS_BC_ISOTHERMAL_WALL || bcs->hi[d] == HGKS_BC_ISOTHERMAL_WALL;
-        if ((bcs->lo[d] != HGKS_BC_PERIODIC && bcs->lo[d] != HGKS_BC_ISOTHERMAL_WALL) ||
-            (bcs->hi[d] != HGKS_BC_PERIODIC && bcs->hi[d] != HGKS_BC_ISOTHERMAL_WALL))
-            return set_err(nullptr, HGKS_ERR_INVALID_ARG, "unknown boundary condition");
+        bool ext = bcs->lo[d] == HGKS_BC_EXTERNAL || bcs->hi[d] == HGKS_BC_EXTERNAL;
+        for (int side = 0; side < 2; side++) {
+            const hgks_bc b = side ? bcs->hi[d] : bcs->lo[d];
+            if (b != HGKS_BC_PERIODIC && b != HGKS_BC_ISOTHERMAL_WALL && b != HGKS_BC_EXTERNAL)
+                return set_err(nullptr, HGKS_ERR_INVALID_ARG, "unknown boundary condition");
+        }
+        if (ext && d != 2)
+            return set_err(nullptr, HGKS_ERR_INVALID_ARG, "EXTERNAL sides are accepted in z only (z slabs)");
         if (wall && n[d] < NG) return set_err(nullptr, HGKS_ERR_INVALID_ARG, "walls need >= 3 cells");
+        if (ext && n[d] < NG)
+            return set_err(nullptr, HGKS_ERR_INVALID_ARG, "EXTERNAL sides need >= 3 cells in their direction");
     }
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
@@ -450,6 +457,94 @@ extern "C" hgks_status hgks_step_dt(hgks_t h, int nsteps, double dt)
     if (!h) return set_err(nullptr, HGKS_ERR_INVALID_ARG, "null handle");
     if (nsteps < 0 || !(dt > 0.0)) return set_err(h, HGKS_ERR_INVALID_ARG, "need nsteps >= 0 and dt > 0");
     return run_steps(h, nsteps, 0.0, dt);
+}
+
+// ---------------------------------------------------------------------------
+// sub-domains: the step in phases (fill, halo exchange by the caller, stage)
+// ---------------------------------------------------------------------------
+static double *state_of(hgks_t h, int state) { return state == HGKS_STATE_CURRENT ? h->q[h->cur] : h->qs; }
+
+extern "C" hgks_status hgks_fill_ghosts(hgks_t h, int state)
+{
+    if (!h) return set_err(nullptr, HGKS_ERR_INVALID_ARG, "null handle");
+    if (state != HGKS_STATE_CURRENT && state != HGKS_STATE_STAGE)
+        return set_err(h, HGKS_ERR_INVALID_ARG, "state must be HGKS_STATE_CURRENT or HGKS_STATE_STAGE");
+    launch_ghost(h->P, state_of(h, state), h->st);
+    CK(h, cudaGetLastError());
+    return HGKS_OK;
+}
+
+extern "C" size_t hgks_halo_count(hgks_t h, int dir)
+{
+    if (!h || dir != 2) return 0;
+    return (size_t)5 * NG * (size_t)h->P.sz;
+}
+
+static hgks_status halo_args(hgks_t h, int state, int dir, int side, const void *buf)
+{
+    if (!h) return set_err(nullptr, HGKS_ERR_INVALID_ARG, "null handle");
+    if (!buf) return set_err(h, HGKS_ERR_INVALID_ARG, "null halo buffer");
+    if (state != HGKS_STATE_CURRENT && state != HGKS_STATE_STAGE)
+        return set_err(h, HGKS_ERR_INVALID_ARG, "state must be HGKS_STATE_CURRENT or HGKS_STATE_STAGE");
+    if (dir != 2) return set_err(h, HGKS_ERR_INVALID_ARG, "halo exchange is supported in z (dir 2) only");
+    if (side != 0 && side != 1) return set_err(h, HGKS_ERR_INVALID_ARG, "side must be 0 (low) or 1 (high)");
+    return HGKS_OK;
+}
+
+extern "C" hgks_status hgks_halo_get(hgks_t h, int state, int dir, int side, double *d_buf)
+{
+    hgks_status s = halo_args(h, state, dir, side, d_buf);
+    if (s) return s;
+    launch_halo_z(h->P, state_of(h, state), side == 0 ? 0 : h->P.n[2] - NG, d_buf, true, h->st);
+    CK(h, cudaGetLastError());
+    return HGKS_OK;
+}
+
+extern "C" hgks_status hgks_halo_set(hgks_t h, int state, int dir, int side, const double *d_buf)
+{
+    hgks_status s = halo_args(h, state, dir, side, d_buf);
+    if (s) return s;
+    launch_halo_z(h->P, state_of(h, state), side == 0 ? -NG : h->P.n[2], const_cast<double *>(d_buf), false, h->st);
+    CK(h, cudaGetLastError());
+    return HGKS_OK;
+}
+
+extern "C" hgks_status hgks_stage(hgks_t h, int stage, double dt)
+{
+    if (!h) return set_err(nullptr, HGKS_ERR_INVALID_ARG, "null handle");
+    if ((stage != 1 && stage != 2) || !(dt > 0.0))
+        return set_err(h, HGKS_ERR_INVALID_ARG, "need stage 1 or 2 and dt > 0");
+    const Params &P = h->P;
+    const double *Fc[3] = { h->F[0], h->F[1], h->F[2] };
+    if (stage == 1) {
+        double *q = h->q[h->cur];
+        launch_dt_final(h->ctl, 0.0, dt, h->st);
+        enqueue_sweeps(h, q, true, nullptr);
+        launch_update(P, 1, q, Fc, h->qs, h->r, h->ctl, h->st);
+        CK(h, cudaGetLastError());
+        h->stage1_done = true;
+        return HGKS_OK;
+    }
+    if (!h->stage1_done) return set_err(h, HGKS_ERR_STATE, "hgks_stage(2) needs stage 1 of the same step first");
+    h->stage1_done = false;
+    launch_dt_final(h->ctl, 0.0, dt, h->st);
+    enqueue_sweeps(h, h->qs, false, nullptr);
+    launch_update(P, 2, h->qs, Fc, h->q[1 - h->cur], h->r, h->ctl, h->st);
+    launch_commit(h->ctl, 1 - h->cur, h->st);
+    h->cur = 1 - h->cur;
+    CK(h, cudaGetLastError());
+    Ctl c;
+    hgks_status st = read_ctl(h, c);
+    if (st) return st;
+    if (c.flag) {
+        h->cur = c.good;
+        c.flag = 0;
+        st = write_ctl(h, c);
+        if (st) return st;
+        return set_err(h, HGKS_ERR_NONFINITE, "a stage produced a non-finite or non-positive state; "
+                                              "state left at the last completed step");
+    }
+    return HGKS_OK;
 }
 
 extern "C" hgks_status hgks_compute_dt(hgks_t h, double cfl, double *dt)

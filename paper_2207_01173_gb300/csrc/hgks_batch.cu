@@ -440,6 +440,12 @@ extern "C" hgks_status hgks_batch_create(hgks_t *handles, int n, hgks_batch_t *o
                 set_global_error("hgks_batch_create: a handle appears twice");
                 return HGKS_ERR_INVALID_ARG;
             }
+        if (h->P.bc_lo[2] == HGKS_BC_EXTERNAL || h->P.bc_hi[2] == HGKS_BC_EXTERNAL) {
+            delete b;
+            set_global_error("hgks_batch_create: a sub-domain handle (EXTERNAL sides) needs its halos set "
+                             "between stages and cannot be stepped in a batch");
+            return HGKS_ERR_INVALID_ARG;
+        }
         b->h.push_back(h);
         Inst in;
         memset(&in, 0, sizeof in);

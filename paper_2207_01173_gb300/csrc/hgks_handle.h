@@ -23,5 +23,6 @@ struct hgks_s {
     double *stat_scratch = nullptr, *stat_out = nullptr;
     hgks::Ctl *ctl = nullptr;
     double rho_ref = 1.0;
+    bool stage1_done = false;  // hgks_stage: stage 1 of the step in progress has run
     std::string err;
 };

@@ -54,6 +54,8 @@ __host__ __device__ inline Box box_face(const Params &P, int d)
 
 // launches (all on `st`)
 void launch_ghost(const Params &P, double *q, cudaStream_t st);
+// three z planes starting at interior layer k0 to (to_buf) or from a buffer [5][3][ny+6][nx+6]
+void launch_halo_z(const Params &P, double *q, int k0, double *buf, bool to_buf, cudaStream_t st);
 void launch_dt_reset(Ctl *ctl, cudaStream_t st);
 void launch_cfl(const Params &P, const double *q, Ctl *ctl, cudaStream_t st);
 void launch_dt_final(Ctl *ctl, double cfl, double fixed_dt, cudaStream_t st);

@@ -24,6 +24,31 @@ void launch_ghost(const Params &P, double *q, cudaStream_t st)
 }
 
 // ---------------------------------------------------------------------------
+// halo layers of a z slab: the three z planes next to a side, whole padded
+// planes (their x / y ghosts included), to or from a caller's buffer
+// [5][3][ny + 6][nx + 6].  get: interior layers k0 .. k0 + 2 -> buffer;
+// set: buffer -> ghost layers.  The planes of one component are contiguous.
+// ---------------------------------------------------------------------------
+__global__ void k_halo_z(Params P, double *q, int k0, double *buf, int to_buf)
+{
+    const long long per_c = 3 * P.sz;  // doubles of one component
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 5 * per_c) return;
+    const int c = (int)(t / per_c);
+    const long long r = t - c * per_c;  // offset within the three planes
+    const long long qi = (long long)c * P.cs + (long long)(k0 + NG) * P.sz + r;
+    if (to_buf) buf[t] = q[qi];
+    else q[qi] = buf[t];
+}
+
+// k0: first of the three z layers (interior index; -3 or nz for the ghosts)
+void launch_halo_z(const Params &P, double *q, int k0, double *buf, bool to_buf, cudaStream_t st)
+{
+    const long long n = 5 * 3 * P.sz;
+    k_halo_z<<<grid_for(n, 256), 256, 0, st>>>(P, q, k0, buf, to_buf ? 1 : 0);
+}
+
+// ---------------------------------------------------------------------------
 // time step: dt = cfl * min over cells, directions of dx_d / (|u_d| + c)
 // ---------------------------------------------------------------------------
 __global__ void k_dt_reset(Ctl *ctl) { ctl->dtmin_bits = 0x7FF0000000000000ull; /* +inf */ }

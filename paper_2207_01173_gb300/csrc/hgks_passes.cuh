@@ -146,6 +146,7 @@ static __device__ __forceinline__ void pos_ghost(const Params &P, double *q, int
     const int side = g / NG, m = g % NG, n = P.n[d];
     const int gi = side == 0 ? -1 - m : n + m;
     const int bc = side == 0 ? P.bc_lo[d] : P.bc_hi[d];
+    if (bc == 2) return;  // EXTERNAL: a neighbouring sub-domain's layers, set by the caller
     int si;
     if (bc == 0) si = ((gi % n) + n) % n;
     else si = side == 0 ? m : n - 1 - m;

@@ -103,6 +103,62 @@ class ZSlabs:
         return t.numpy()
 
 
+# ---------------------------------------------------------------------------
+# several slabs of one domain in one process (one device): each slab is a
+# solver handle with EXTERNAL z sides, and its halos travel device to device
+# through caller-owned buffers.  This is the same exchange as ZSlabs's, run
+# without a process group, so that the decomposition of the CUDA path can be
+# checked on a single GPU against the undivided run.
+# ---------------------------------------------------------------------------
+def exchange_local_slabs(solvers, state, bufs):
+    """Fill the z ghost layers of `state` on every slab from its neighbours
+    (periodic ring in z).  solvers: slab handles ordered by z; bufs: per slab
+    a pair (lo, hi) of device buffers of solver.halo_count() doubles each,
+    given as integer device pointers."""
+    k = len(solvers)
+    for sv in solvers:
+        sv.fill_ghosts(state)  # x / y ghosts first: they travel with the planes
+    for sv, (lo, hi) in zip(solvers, bufs):
+        sv.halo_get(state, 0, lo)
+        sv.halo_get(state, 1, hi)
+    for i, sv in enumerate(solvers):
+        sv.halo_set(state, 0, bufs[(i - 1) % k][1])  # low ghosts: the lower slab's top layers
+        sv.halo_set(state, 1, bufs[(i + 1) % k][0])  # high ghosts: the upper slab's bottom layers
+
+
+def step_local_slabs(solvers, bufs, nsteps, cfl):
+    """nsteps steps of the decomposed domain: the global CFL time step (the
+    minimum over slabs), then per stage the halo exchange and the stage on
+    every slab (Alg. 2).  Returns the time steps taken."""
+    dts = []
+    for _ in range(nsteps):
+        dt = min(sv.compute_dt(cfl) for sv in solvers)
+        for stage in (1, 2):
+            exchange_local_slabs(solvers, stage - 1, bufs)
+            for sv in solvers:
+                sv.stage(stage, dt)
+        dts.append(dt)
+    return dts
+
+
+def local_slab_stats(solvers, bufs, lz):
+    """Diagnostics of the whole domain from its slabs: volume averages
+    weighted by each slab's z length (lz: per slab), sums added, the Mach
+    number maximised; the halos of the current state are exchanged first
+    because the vorticity stencils reach into them."""
+    exchange_local_slabs(solvers, 0, bufs)
+    st = [sv.stats() for sv in solvers]
+    L = float(sum(lz))
+    out = dict(st[0])
+    for k in ("Ek", "enstrophy", "eps_com", "wall_shear"):
+        out[k] = sum(s[k] * l for s, l in zip(st, lz)) / L
+    for k in ("mass", "energy"):
+        out[k] = sum(s[k] for s in st)
+    out["mom"] = [sum(s["mom"][c] for s in st) for c in range(3)]
+    out["max_mach"] = max(s["max_mach"] for s in st)
+    return out
+
+
 def reduce_scalar(x, op, group=None, device="cpu"):
     if not dist.is_initialized() or dist.get_world_size(group) == 1:
         return float(x)

@@ -14,7 +14,8 @@ import numpy as np
 from . import build as _build
 
 HGKS_OK, HGKS_ERR_INVALID_ARG, HGKS_ERR_OOM, HGKS_ERR_CUDA, HGKS_ERR_NONFINITE, HGKS_ERR_TIMEOUT, HGKS_ERR_STATE = range(7)
-BC_PERIODIC, BC_WALL = 0, 1
+BC_PERIODIC, BC_WALL, BC_EXTERNAL = 0, 1, 2
+STATE_CURRENT, STATE_STAGE = 0, 1
 VISC_CONSTANT, VISC_POWER = 0, 1
 FP64, MIXED = 0, 1
 
@@ -92,7 +93,8 @@ EXPORTS = ("hgks_create", "hgks_init_tgv", "hgks_init_channel", "hgks_init_densi
            "hgks_stats", "hgks_footprint_bytes", "hgks_last_error", "hgks_synchronize", "hgks_destroy",
            "hgks_step_timed", "hgks_fp64_probe", "hgks_flop_model", "hgks_cfl_dt_noalloc",
            "hgks_batch_create", "hgks_batch_step", "hgks_batch_tune", "hgks_batch_steps", "hgks_batch_info",
-           "hgks_batch_last_error", "hgks_batch_destroy")
+           "hgks_batch_last_error", "hgks_batch_destroy", "hgks_fill_ghosts", "hgks_halo_count", "hgks_halo_get",
+           "hgks_halo_set", "hgks_stage")
 
 
 def library_path():
@@ -142,9 +144,15 @@ def lib(build_if_missing=True):
         L.hgks_batch_last_error.restype = C.c_char_p
         L.hgks_batch_destroy.argtypes = [C.c_void_p]
         L.hgks_batch_destroy.restype = None
+        L.hgks_fill_ghosts.argtypes = [C.c_void_p, C.c_int]
+        L.hgks_halo_count.argtypes = [C.c_void_p, C.c_int]
+        L.hgks_halo_count.restype = C.c_size_t
+        L.hgks_halo_get.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p]
+        L.hgks_halo_set.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p]
+        L.hgks_stage.argtypes = [C.c_void_p, C.c_int, C.c_double]
         for name in EXPORTS:
             if name not in ("hgks_footprint_bytes", "hgks_last_error", "hgks_destroy", "hgks_batch_last_error",
-                            "hgks_batch_destroy"):
+                            "hgks_batch_destroy", "hgks_halo_count"):
                 getattr(L, name).restype = S
         _lib = L
     return _lib
@@ -309,6 +317,25 @@ class Solver:
 
     def synchronize(self):
         self._check(lib().hgks_synchronize(self.h))
+
+    # -- sub-domains (EXTERNAL z sides): the step in phases ---------------
+    def fill_ghosts(self, state=STATE_CURRENT):
+        self._check(lib().hgks_fill_ghosts(self.h, state))
+
+    def halo_count(self, dir=2):
+        """Doubles of one halo buffer of direction dir ([5][3][ny+6][nx+6] for z)."""
+        return int(lib().hgks_halo_count(self.h, dir))
+
+    def halo_get(self, state, side, d_buf, dir=2):
+        """Three boundary layers of `side` (0 low, 1 high) into device pointer d_buf (int)."""
+        self._check(lib().hgks_halo_get(self.h, state, dir, side, C.c_void_p(d_buf)))
+
+    def halo_set(self, state, side, d_buf, dir=2):
+        """Device buffer d_buf (int) into the three ghost layers of `side`."""
+        self._check(lib().hgks_halo_set(self.h, state, dir, side, C.c_void_p(d_buf)))
+
+    def stage(self, stage, dt):
+        self._check(lib().hgks_stage(self.h, stage, dt))
 
     def _host_ptr(self, a, writable):
         size = int(np.prod(self.shape))

@@ -59,6 +59,16 @@ def test_invalid_arguments_rejected_before_device():
     with pytest.raises(hgks.HgksError) as e:
         hgks.Solver((8, 2, 8), bc_lo=(0, 1, 0), bc_hi=(0, 1, 0))
     assert e.value.status == hgks.HGKS_ERR_INVALID_ARG
+    # sub-domain sides: z only, and at least three planes
+    with pytest.raises(hgks.HgksError) as e:
+        hgks.Solver((8, 8, 8), bc_lo=(2, 0, 0), bc_hi=(2, 0, 0))
+    assert e.value.status == hgks.HGKS_ERR_INVALID_ARG and "z only" in str(e.value)
+    with pytest.raises(hgks.HgksError) as e:
+        hgks.Solver((8, 8, 2), bc_lo=(0, 0, 2), bc_hi=(0, 0, 2))
+    assert e.value.status == hgks.HGKS_ERR_INVALID_ARG
+    with pytest.raises(hgks.HgksError) as e:
+        hgks.Solver((8, 8, 8), bc_lo=(0, 0, 3), bc_hi=(0, 0, 0))
+    assert e.value.status == hgks.HGKS_ERR_INVALID_ARG and "unknown" in str(e.value)
 
 
 def test_batch_workload_is_seeded_and_in_range():
