@@ -44,16 +44,16 @@ GAMMA = 1.4
 MA, RE, PR, OMEGA, CFL = 0.1, 1600.0, 0.72, 0.7, 0.5
 METRIC = "cell-updates/s TGV 256^3 FP64 vs mixed at stated error; serve p50/p99 ms"
 # DRAM bytes per face of one k_flux launch (dram__bytes_read.sum +
-# dram__bytes_write.sum from an ncu capture of k_flux on TGV 64^3, 278.7 MB
-# for 266,240 faces), scaled by the faces of a launch.  k_flux has been
-# rebuilt since that capture (the face geometry moved into a shared helper:
-# the same arithmetic and accesses, 48 instead of 56 bytes of spills per
-# thread), so the roofline's traffic is reported as null and the earlier
-# figure rides along as traffic_previous_build until the next capture.
-K_FLUX_DRAM_BYTES_PER_FACE = 278708480 / 266240
-K_FLUX_TRAFFIC_CURRENT = False
-# the same for k_flux_mx (196.4 MB for 266,240 faces of TGV 64^3)
-K_FLUX_MX_DRAM_BYTES_PER_FACE = 196355328 / 266240
+# dram__bytes_write.sum, mean of the 30 k_flux launches of an ncu capture of
+# `bench.py --n 128 --steps 1 --warmup 3` on the current build: 3342 MB read +
+# 306 MB written for 2,113,536 faces), scaled by the faces of a launch.  The
+# 128^3 input of the pass (1.9 GB of first-tangential records) is 15x the L2,
+# so the per-face figure carries over to 256^3 (at 64^3, where the input is
+# only twice the L2, a launch moved 1.02 instead of 1.73 kB per face).
+K_FLUX_DRAM_BYTES_PER_FACE = (3341.87e6 + 306.34e6) / 2113536
+K_FLUX_TRAFFIC_CURRENT = True
+# the same for k_flux_mx (2012 MB read + 170 MB written per 128^3 launch)
+K_FLUX_MX_DRAM_BYTES_PER_FACE = (2012.23e6 + 170.33e6) / 2113536
 # GB300 FP32 (non-tensor) peak: 152 SMs x 128 FP32 lanes x 2 flops per FMA x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # Table 3 of the paper: 256^3 TGV, FP64, Tesla V100, 11.697 h for 20 t_c at dt = 8.925e-4
@@ -204,7 +204,7 @@ def batched_leg(hg, args, stream):
     out = {"workload": "64 Taylor-Green vortices, each grid dimension drawn from {24,32,48,64,96}, Ma U[0.1,0.5], "
                        "Re log-U[400,3200], seed 64, CFL %.1f" % CFL,
            "problems": len(probs), "cells": cells}
-    for prec, name, steps in ((hg.FP64, "fp64", args.batch_steps), (hg.MIXED, "mixed", 2 * args.batch_steps)):
+    for prec, name, steps in ((hg.FP64, "fp64", args.batch_steps), (hg.MIXED, "mixed", args.batch_steps)):
         solvers = [hg.Solver(n, precision=prec, **workloads.tgv_solver_kwargs(Ma, Re)) for n, Ma, Re in probs]
 
         def init():
@@ -244,8 +244,9 @@ def batched_leg(hg, args, stream):
                      "sequential_value": cells * steps / (seq_ms * 1e-3),
                      "speedup_vs_sequential": seq_ms / bat_ms,
                      "bitwise_equal_to_sequential": bool(same),
-                     "tile_sweep": info["tile_sweep"], "tile_cells": info["tile_cells"],
-                     "tuned_step_ms": tune_ms, "launches_per_step": info["launches_per_step"],
+                     "tiles_chosen": {k: info[k] for k in ("tile_cells", "tile_normal", "tile_tan1", "tile_sweep",
+                                                           "tile_normal_mx")},
+                     "tuned_passes_ms": tune_ms, "launches_per_step": info["launches_per_step"],
                      "gpu_launches": info["launches_per_step"] * steps, "tiles": info["tiles"],
                      "clocks": clk.summary()}
     return out
@@ -279,6 +280,8 @@ def serve_leg(hg, args, capacity):
                 arrival_rate_per_s=rate, capacity_cell_updates_per_s=capacity, mean_work_cell_updates=mean_work,
                 max_chunk=args.serve_chunk, policy=args.serve_policy, age_s=args.serve_age,
                 batch_rebuilds=eng.rebuilds,
+                batch_rebuild_create_s=eng.rebuild_create_s,
+                batch_rebuild_capture_s=eng.rebuild_capture_s,
                 clocks=clk.summary(),
                 latency_percentiles="numpy linear interpolation over completed requests")
     return summ
@@ -351,11 +354,17 @@ def run_ours(args, rank, world, local_rank):
     # CPU baseline first (no GPU context yet), rank 0 only, N = 1 only
     cpu_baseline = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, el = oracle_rate(args.cpu_steps, args.ref_n)
-        cpu_baseline = {"value": rate, "unit": "cell-updates/s", "cores": oracle_threads(), "kind": "oracle",
+        # two samples: 32^3 (its 2.2 MB state buffers sit in the host caches)
+        # and 64^3 (14 MB state buffers, 0.5 GB of face records per sweep,
+        # beyond the caches, like 256^3); the 64^3 rate is the reported value
+        rate32, el32 = oracle_rate(args.cpu_steps, args.ref_n)
+        rate64, el64 = oracle_rate(1, 64)
+        cpu_baseline = {"value": rate64, "unit": "cell-updates/s", "cores": oracle_threads(), "kind": "oracle",
                         "cpu_model": host_cpu_model(),
-                        "sample": "TGV %d^3, %d steps after 1 untimed (same per-cell work as %d^3), %.1f s"
-                                  % (args.ref_n, args.cpu_steps, args.n, el)}
+                        "sample": "TGV 64^3, 1 step after 1 untimed (%.1f s; per-cell work equals the %d^3 "
+                                  "grid's, working set beyond the host caches); beside it TGV %d^3, %d steps "
+                                  "after 1 untimed (%.1f s)" % (el64, args.n, args.ref_n, args.cpu_steps, el32),
+                        "value_32": rate32, "ratio_64_over_32": rate64 / rate32}
 
     torch.cuda.set_device(local_rank)
     import paper_2207_01173_gb300 as hg
@@ -431,11 +440,31 @@ def run_ours(args, rank, world, local_rank):
         ach = fl_flops / (fl_ms * 1e-3) / 1e12
         mixed["roofline"] = {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                              "frac": ach / FP32_PEAK_TFLOPS, "traffic": K_FLUX_MX_DRAM_BYTES_PER_FACE * (n + 1) * n * n,
-                             "traffic_note": "ncu DRAM bytes of one TGV 64^3 launch scaled by faces",
+                             "traffic_note": "ncu DRAM bytes per k_flux_mx launch on TGV 128^3 scaled by faces",
                              "kernel": "k_flux_mx",
                              "peak_note": "FP32 FMA peak from unit counts and clock: 152 SMs x 128 lanes x 2 "
                                           "flops x 2.07 GHz",
                              "algorithmic_flops_per_launch": fl_flops, "avg_launch_ms": fl_ms}
+        # the same with the Maxwellian temperature, collision time and time
+        # coefficients of every Gauss point in FP64 (HGKS_MIXED_T64): its cost
+        # and its error beside the FP32 split's
+        if not args.no_t64:
+            m64 = hg.Solver((n, n, n), precision=hg.MIXED_T64, **tgv_kwargs())
+            m64.init_tgv(MA, 1.0, 1.0)
+            ms_t, times_t, clocks_t = timed_run(m64)
+            qt = m64.get_state()
+            st_t = m64.stats()
+            m64.close()
+            inst_t = float((np.abs(qt - q64).reshape(5, -1).max(axis=1) / scale).max())
+            del qt
+            mixed["t64_variant"] = {
+                "value": world * cells * args.steps / (ms_t * 1e-3), "unit": "cell-updates/s",
+                "ms_per_step": ms_t / args.steps, "cost_vs_mixed": ms_t / ms_mx,
+                "flux_ms_per_step": sum(t["flux_ms"] for t in times_t) / args.steps,
+                "error_vs_fp64": {"steps": args.warmup + args.steps, "instantaneous_rel_linf": inst_t,
+                                  "Ek_rel": abs(st_t["Ek"] - s64["Ek"]) / abs(s64["Ek"]),
+                                  "enstrophy_rel": abs(st_t["enstrophy"] - s64["enstrophy"]) / abs(s64["enstrophy"])},
+                "clocks": clocks_t}
     del q64
 
     # end to end through the public API with host buffers: pinned H2D of the
@@ -484,9 +513,8 @@ def run_ours(args, rank, world, local_rank):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
                      "traffic": K_FLUX_DRAM_BYTES_PER_FACE * faces_per_launch if K_FLUX_TRAFFIC_CURRENT else None,
-                     "traffic_previous_build": K_FLUX_DRAM_BYTES_PER_FACE * faces_per_launch,
-                     "traffic_note": "ncu DRAM bytes of one TGV 64^3 launch scaled by faces; null because k_flux "
-                                     "was rebuilt after that capture (same accesses, fewer spills)", "kernel": "k_flux",
+                     "traffic_note": "ncu DRAM bytes per k_flux launch on TGV 128^3 (mean of 30 launches, current "
+                                     "build) scaled by faces to one 256^3 launch", "kernel": "k_flux",
                      "peak_note": "nominal GB300 dense FP64 (1.25 TFLOP/s); measured FP64 FMA probe %.3f TFLOP/s"
                                   % fp64_peak,
                      "algorithmic_flops_per_launch": flops_per_launch,
@@ -522,8 +550,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
-    ap.add_argument("--batch-steps", type=int, default=3)
-    ap.add_argument("--serve-requests", type=int, default=12)
+    ap.add_argument("--no-t64", action="store_true", help="skip the HGKS_MIXED_T64 variant of the mixed leg")
+    ap.add_argument("--batch-steps", type=int, default=50)
+    ap.add_argument("--serve-requests", type=int, default=100)
     ap.add_argument("--serve-budget-gb", type=float, default=96.0)
     ap.add_argument("--serve-chunk", type=int, default=8)
     ap.add_argument("--histories", type=int, default=0,

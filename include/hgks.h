@@ -67,8 +67,14 @@ typedef enum { HGKS_VISC_CONSTANT = 0, HGKS_VISC_POWER = 1 } hgks_visc_kind;
  * Q0 (mean of the two sides plus an FP32 compatibility correction), its
  * pressure and Euler flux as float-float pairs (two FP32 numbers, ~48 bits).
  * A MIXED handle allocates one more state-sized buffer (the state split into
- * hi / lo FP32 planes before each stage). */
-typedef enum { HGKS_FP64 = 0, HGKS_MIXED = 1 } hgks_precision;
+ * hi / lo FP32 planes before each stage).
+ * HGKS_MIXED_T64: HGKS_MIXED with the Maxwellian temperature T0 = p0/rho0 of
+ * every Gauss point, its collision time tau = mu(T0)/p0 and the time-
+ * integration coefficients (the exp(-delta/tau) terms of both windows) formed
+ * in FP64 from the float-float Q0; the sums they weight stay FP32.  This is
+ * the split that keeps the temperature / collision-time terms in FP64; it is
+ * not accepted by hgks_batch_create. */
+typedef enum { HGKS_FP64 = 0, HGKS_MIXED = 1, HGKS_MIXED_T64 = 2 } hgks_precision;
 
 /* Structured grid (Sec. 2 "orthogonal structured mesh"; Sec. 4.2 mesh map).
  * nx, ny, nz >= 1 cells.  Uniform spacing lx/nx and lz/nz in x and z.
@@ -122,7 +128,7 @@ typedef struct {
  *   derivative (0, G L_rho, G.L_mom); the interface flux's time slope comes
  *   from the force-free compatibility condition, so the forced terms are
  *   second order in time.
- *   precision: HGKS_FP64 or HGKS_MIXED (see hgks_precision).
+ *   precision: HGKS_FP64, HGKS_MIXED or HGKS_MIXED_T64 (see hgks_precision).
  *   cuda_stream: a cudaStream_t, or NULL.
  *   out: receives the handle.
  * Errors: INVALID_ARG, OOM, CUDA (no device / context failure). */
@@ -338,17 +344,20 @@ hgks_status hgks_cfl_dt_noalloc(const hgks_grid *grid, double gamma, double cfl,
 typedef struct hgks_batch_s *hgks_batch_t;
 typedef struct {
     int problems;          /* handles in the batch */
-    int tile_sweep;        /* interface positions per tile of the sweep passes */
-    int tile_cells;        /* cells per tile of the cell passes */
+    int tile_sweep;        /* interface positions per tile of the FP64 flux pass */
+    int tile_cells;        /* cells per tile of the cell passes (ghost fill, CFL, update, split) */
     int launches_per_step; /* kernel nodes of the per-step graph */
     long long tiles;       /* tiles over all passes */
     double last_ms;        /* device time of the graph steps of the last hgks_batch_step call */
     int last_steps;        /* steps of that call */
+    int tile_normal;       /* positions per tile of the FP64 normal pass */
+    int tile_tan1;         /* positions per tile of the FP64 first tangential pass */
+    int tile_normal_mx;    /* positions per tile of the mixed normal pass */
 } hgks_batch_info_t;
 /* handles: n distinct handles on one stream (n >= 1).  *out receives the
  * batch.  Errors: INVALID_ARG (NULL, n < 1, a repeated handle, handles on
- * different streams, a handle with EXTERNAL sides), CUDA (allocation of the
- * work-lists). */
+ * different streams, a handle with EXTERNAL sides or HGKS_MIXED_T64
+ * precision), CUDA (allocation of the work-lists). */
 hgks_status hgks_batch_create(hgks_t *handles, int n, hgks_batch_t *out);
 /* nsteps (>= 0) steps of every problem, each with its own CFL time step
  * cfl * min over cells of dx_d / (|u_d| + c).  Work queued earlier on the
@@ -357,12 +366,18 @@ hgks_status hgks_batch_create(hgks_t *handles, int n, hgks_batch_t *out);
  * cfl or the tile size changes.  Errors: INVALID_ARG, NONFINITE (see above),
  * CUDA. */
 hgks_status hgks_batch_step(hgks_batch_t b, int nsteps, double cfl);
-/* Autotuner: for each candidate sweep tile size (256, 1024, 4096, 16384
- * positions) one warm-up and one timed graph step on the current states;
- * keeps the fastest and restores every state and control block, so the
- * problems are where they were.  Allocates a copy of the states for the
- * duration of the call.  best_ms (may be NULL) receives the best step time.
- * Errors: INVALID_ARG, CUDA. */
+/* Autotuner: picks the tile size of each tunable pass by timing that pass
+ * on the current states: the cell passes (candidates 2048, 8192, 32768
+ * cells per tile) and, for each precision present, the normal, first
+ * tangential (FP64) and flux (FP64) sweeps (candidates 256, 1024, 4096,
+ * 16384 positions), one group after the other, each candidate timed once
+ * after a warm-up run.  A timing run enqueues the ghost fill, the CFL
+ * reduction, the state split and the sweeps of direction x: they write only
+ * ghost cells (with the values they hold), the CFL minimum and scratch
+ * buffers, so the problems stay where they were and nothing is allocated
+ * but the tile lists.  best_ms (may be NULL) receives the summed time of the
+ * tuned groups in one such run.  The chosen sizes are reported by
+ * hgks_batch_info. */
 hgks_status hgks_batch_tune(hgks_batch_t b, double cfl, double *best_ms);
 /* steps[i] receives the step counter of problem i as read back at the end
  * of the last hgks_batch_step call (no device work); a problem that stopped

@@ -94,7 +94,7 @@ extern "C" size_t hgks_footprint_bytes(const hgks_grid *grid, hgks_precision pre
     Params P = shape_params(*grid);
     Sizes s = sizes_of(P);
     size_t doubles = 4 * s.pad + s.fq + s.t1 + s.F[0] + s.F[1] + s.F[2] + 2 * s.cells + s.ytab + s.stats;
-    if (precision == HGKS_MIXED) doubles += s.pad;  // the split state
+    if (precision == HGKS_MIXED || precision == HGKS_MIXED_T64) doubles += s.pad;  // the split state
     return doubles * sizeof(double) + sizeof(Ctl);
 }
 
@@ -127,8 +127,9 @@ extern "C" hgks_status hgks_create(const hgks_grid *grid, double gamma, double P
     if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1 || !(grid->lx > 0) || !(grid->ly > 0) || !(grid->lz > 0))
         return set_err(nullptr, HGKS_ERR_INVALID_ARG, "grid sizes must be positive");
     if (!(gamma > 1.0) || !(Pr > 0.0)) return set_err(nullptr, HGKS_ERR_INVALID_ARG, "need gamma > 1 and Pr > 0");
-    if (precision != HGKS_FP64 && precision != HGKS_MIXED)
-        return set_err(nullptr, HGKS_ERR_INVALID_ARG, "precision must be HGKS_FP64 or HGKS_MIXED");
+    if (precision != HGKS_FP64 && precision != HGKS_MIXED && precision != HGKS_MIXED_T64)
+        return set_err(nullptr, HGKS_ERR_INVALID_ARG, "precision must be HGKS_FP64, HGKS_MIXED or HGKS_MIXED_T64");
+    const bool mixed = precision != HGKS_FP64;
     if (visc->kind == HGKS_VISC_POWER && !(visc->T_ref > 0.0))
         return set_err(nullptr, HGKS_ERR_INVALID_ARG, "power-law viscosity needs T_ref > 0");
     if (!(visc->mu_ref >= 0.0)) return set_err(nullptr, HGKS_ERR_INVALID_ARG, "mu_ref must be >= 0");
@@ -197,9 +198,9 @@ extern "C" hgks_status hgks_create(const hgks_grid *grid, double gamma, double P
     if (!st) st = alloc(&h->r, s.pad);
     if (!st) st = alloc(&h->fq, s.fq);
     if (!st) st = alloc(&h->t1, s.t1);
-    if (!st && precision == HGKS_MIXED) st = alloc(&h->qf, s.pad);
+    if (!st && mixed) st = alloc(&h->qf, s.pad);
     if (!st) st = cuda_check(h, fp64_setup(), "flux kernel set-up");
-    if (!st && precision == HGKS_MIXED) st = cuda_check(h, mixed_setup(), "mixed-precision kernel set-up");
+    if (!st && mixed) st = cuda_check(h, mixed_setup(), "mixed-precision kernel set-up");
     for (int d = 0; d < 3 && !st; d++) st = alloc(&h->F[d], s.F[d]);
     if (!st) st = alloc(&h->io[0], s.cells);
     if (!st) st = alloc(&h->io[1], s.cells);
@@ -371,19 +372,19 @@ static void mark(StepTimer *T, int kind, int nlaunch = 1)
 static void enqueue_sweeps(hgks_t h, const double *q, bool record_wall, StepTimer *T)
 {
     const Params &P = h->P;
-    const bool mixed = h->prec == HGKS_MIXED;
+    const bool mixed = h->prec != HGKS_FP64, t64 = h->prec == HGKS_MIXED_T64;
     if (mixed) {
         launch_split_mixed(P, q, h->qf, h->ctl, h->st);
         mark(T, TK_OTHER);
     }
     for (int d = 0; d < 3; d++) {
-        if (mixed) launch_sweep_mixed(P, d, h->qf, h->fq, h->t1, h->F[d], h->ctl, h->st, 0);
+        if (mixed) launch_sweep_mixed(P, d, h->qf, h->fq, h->t1, h->F[d], h->ctl, h->st, 0, t64);
         else launch_normal(P, d, q, h->fq, h->ctl, h->st);
         mark(T, TK_NORMAL);
-        if (mixed) launch_sweep_mixed(P, d, h->qf, h->fq, h->t1, h->F[d], h->ctl, h->st, 1);
+        if (mixed) launch_sweep_mixed(P, d, h->qf, h->fq, h->t1, h->F[d], h->ctl, h->st, 1, t64);
         else launch_tan1(P, d, h->fq, h->t1, h->ctl, h->st);
         mark(T, TK_TAN1);
-        if (mixed) launch_sweep_mixed(P, d, h->qf, h->fq, h->t1, h->F[d], h->ctl, h->st, 2);
+        if (mixed) launch_sweep_mixed(P, d, h->qf, h->fq, h->t1, h->F[d], h->ctl, h->st, 2, t64);
         else launch_flux(P, d, h->t1, h->F[d], h->ctl, h->st);
         mark(T, TK_FLUX);
         if (d == 1 && record_wall && (P.bc_lo[1] == HGKS_BC_ISOTHERMAL_WALL || P.bc_hi[1] == HGKS_BC_ISOTHERMAL_WALL)) {

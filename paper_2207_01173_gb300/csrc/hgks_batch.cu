@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(FLUX_MX_BLOCK, 3) kb_flux_mx(const Inst *__res
     const Inst &in = I[tl.inst];
     if (in.ctl->flag) return;
     const Box Bf = box_face(in.P, d), Bt = box_t1(in.P, d);
-    flux_mx_tile(in.P, d, Bf, Bt, t1_mx(in.t1, box_count(Bt)), in.F[d], in.ctl->dt, tl.start, gp_sm);
+    flux_mx_tile<false>(in.P, d, Bf, Bt, t1_mx(in.t1, box_count(Bt)), in.F[d], in.ctl->dt, tl.start, gp_sm);
 }
 
 __global__ void __launch_bounds__(FLUX_BLOCK, 2) kb_flux(const Inst *__restrict__ I, const Tile *__restrict__ T,
@@ -292,7 +292,7 @@ struct hgks_batch_s {
     std::vector<Inst> inst;
     Tile *d_tiles = nullptr;
     int off[WL_N], cnt[WL_N];
-    long long tile_sweep = 2048, tile_cells = 8192;
+    long long tile[WL_N];  // positions (or cells) per tile of each work-list
     int blocks_cells = 0, sms = 0;
     int bsweep[2][3] = {};  // resident blocks of the normal, tan1 and flux kernels, per precision
     bool any_walls = false;
@@ -332,17 +332,17 @@ static hgks_status build_tiles(hgks_batch_t b)
         b->off[w] = (int)all.size();
         for (int i = 0; i < (int)b->inst.size(); i++) {
             const Params &P = b->inst[i].P;
-            if (w < 3) add(w, i, ghost_count(P, w), b->tile_cells);
-            else if (w == WL_CELLS) add(w, i, P.ncell, b->tile_cells);
+            if (w < 3) add(w, i, ghost_count(P, w), b->tile[w]);
+            else if (w == WL_CELLS) add(w, i, P.ncell, b->tile[w]);
             else if (w == WL_PAD) {
-                if (b->inst[i].mixed) add(w, i, P.cs, b->tile_cells);
+                if (b->inst[i].mixed) add(w, i, P.cs, b->tile[w]);
             } else {
                 const int mixed = (w - WL_SWEEP) / 9, pass = (w - WL_SWEEP) / 3 % 3, d = (w - WL_SWEEP) % 3;
                 if (mixed != b->inst[i].mixed) continue;
                 const Box B = pass == 0 ? box_fq(P, d) : pass == 1 ? box_t1(P, d) : box_face(P, d);
                 if (mixed && pass == 2) add(w, i, flux_tiling(P, d).count, 1);  // one entry per flux tile
                 else if (mixed && pass == 1) add(w, i, box_count(B), MX_TILE);   // one block per tile
-                else add(w, i, box_count(B), b->tile_sweep);
+                else add(w, i, box_count(B), b->tile[w]);
             }
         }
         b->cnt[w] = (int)all.size() - b->off[w];
@@ -440,6 +440,12 @@ extern "C" hgks_status hgks_batch_create(hgks_t *handles, int n, hgks_batch_t *o
                 set_global_error("hgks_batch_create: a handle appears twice");
                 return HGKS_ERR_INVALID_ARG;
             }
+        if (h->prec == HGKS_MIXED_T64) {
+            delete b;
+            set_global_error("hgks_batch_create: HGKS_MIXED_T64 handles are stepped alone (the batch runs "
+                             "HGKS_FP64 and HGKS_MIXED problems)");
+            return HGKS_ERR_INVALID_ARG;
+        }
         if (h->P.bc_lo[2] == HGKS_BC_EXTERNAL || h->P.bc_hi[2] == HGKS_BC_EXTERNAL) {
             delete b;
             set_global_error("hgks_batch_create: a sub-domain handle (EXTERNAL sides) needs its halos set "
@@ -495,6 +501,7 @@ extern "C" hgks_status hgks_batch_create(hgks_t *handles, int n, hgks_batch_t *o
     for (int m = 0; m < 2; m++)
         for (int p = 0; p < 3; p++) b->bsweep[m][p] = std::max(1, nb[m][p]) * b->sms;
     b->blocks_cells = b->sms * 8;
+    for (int w = 0; w < WL_N; w++) b->tile[w] = w < WL_SWEEP || w == WL_PAD ? 8192 : 2048;
     e = cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev[0]);
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev[1]);
@@ -593,8 +600,11 @@ extern "C" hgks_status hgks_batch_info(hgks_batch_t b, hgks_batch_info_t *out)
 {
     if (!b || !out) return HGKS_ERR_INVALID_ARG;
     out->problems = (int)b->h.size();
-    out->tile_sweep = (int)b->tile_sweep;
-    out->tile_cells = (int)b->tile_cells;
+    out->tile_sweep = (int)b->tile[wl_sweep(0, 2, 0)];
+    out->tile_cells = (int)b->tile[WL_CELLS];
+    out->tile_normal = (int)b->tile[wl_sweep(0, 0, 0)];
+    out->tile_tan1 = (int)b->tile[wl_sweep(0, 1, 0)];
+    out->tile_normal_mx = (int)b->tile[wl_sweep(1, 0, 0)];
     // ghost 6, dt 3, update 2, commit 1, wall 0/1, split 2 when a mixed
     // problem is present, and 3 sweep passes x 3 directions x 2 stages for
     // each precision present
@@ -609,76 +619,130 @@ extern "C" hgks_status hgks_batch_info(hgks_batch_t b, hgks_batch_info_t *out)
     return HGKS_OK;
 }
 
-// time whole graph steps for each candidate tile size on copies of the
-// states, keep the fastest, restore the states
+// ---------------------------------------------------------------------------
+// autotuner: the tile size of each tunable pass, chosen by timing that pass.
+// Groups of work-lists share one tile size: the cell passes (ghost fill,
+// CFL reduction, state split), and per precision the normal, first
+// tangential and flux sweeps (the mixed first-tangential and flux passes run
+// one block per tile of a fixed shape and are not tuned).  Each timing run
+// enqueues the stage-1 ghost fill, CFL reduction and state split, then the
+// sweep passes of direction x, with events between the groups.  These
+// kernels write only ghost cells (with the values they already hold), the
+// CFL minimum (reset at the start of every step) and scratch buffers, so the
+// problems' states stay where they were and nothing needs to be copied.
+// ---------------------------------------------------------------------------
+enum { TG_CELLS = 0, TG_NORMAL64, TG_TAN64, TG_FLUX64, TG_NORMALMX, TG_N };
+
+static void tg_lists(int g, std::vector<int> &w)
+{
+    w.clear();
+    if (g == TG_CELLS) {
+        for (int d = 0; d < 3; d++) w.push_back(WL_GHOST + d);
+        w.push_back(WL_CELLS);
+        w.push_back(WL_PAD);
+    } else {
+        const int mx = g == TG_NORMALMX, pass = g == TG_NORMAL64 || g == TG_NORMALMX ? 0 : g == TG_TAN64 ? 1 : 2;
+        for (int d = 0; d < 3; d++) w.push_back(wl_sweep(mx, pass, d));
+    }
+}
+
+// one timing run: ms[g] receives the device time of group g's kernels
+static cudaError_t time_groups(hgks_batch_t b, cudaEvent_t *ev, float ms[TG_N])
+{
+    const Inst *I = b->d_inst;
+    cudaStream_t st = b->st;
+    auto T = [&](int w) { return b->d_tiles + b->off[w]; };
+    int k = 0, mark[TG_N + 1];
+    for (int g = 0; g <= TG_N; g++) mark[g] = -1;
+    cudaEventRecord(ev[k++], st);
+    for (int d = 0; d < 3; d++) kb_ghost<<<pgrid(b->cnt[WL_GHOST + d], b->blocks_cells), 256, 0, st>>>(
+        I, T(WL_GHOST + d), b->cnt[WL_GHOST + d], d, 0);
+    kb_cfl<<<pgrid(b->cnt[WL_CELLS], b->blocks_cells), 256, 0, st>>>(I, T(WL_CELLS), b->cnt[WL_CELLS]);
+    if (b->cnt[WL_PAD])
+        kb_split<<<pgrid(b->cnt[WL_PAD], b->blocks_cells), 256, 0, st>>>(I, T(WL_PAD), b->cnt[WL_PAD], 0);
+    mark[TG_CELLS] = k;
+    cudaEventRecord(ev[k++], st);
+    const int d = 0;
+    for (int mx = 0; mx < 2; mx++) {
+        const int wn = wl_sweep(mx, 0, d), wt = wl_sweep(mx, 1, d), wf = wl_sweep(mx, 2, d);
+        if (!b->cnt[wn]) continue;
+        if (mx) {
+            kb_normal<true><<<pgrid(b->cnt[wn], b->bsweep[1][0]), 128, 0, st>>>(I, T(wn), b->cnt[wn], d, 0);
+            mark[TG_NORMALMX] = k;
+            cudaEventRecord(ev[k++], st);
+            kb_tan1_mx<<<(unsigned)b->cnt[wt], MX_TILE, 0, st>>>(I, T(wt), b->cnt[wt], d);
+            kb_flux_mx<<<(unsigned)b->cnt[wf], FLUX_MX_BLOCK, FLUX_MX_TILE_SMEM, st>>>(I, T(wf), b->cnt[wf], d);
+            cudaEventRecord(ev[k++], st);
+        } else {
+            kb_normal<false><<<pgrid(b->cnt[wn], b->bsweep[0][0]), 128, 0, st>>>(I, T(wn), b->cnt[wn], d, 0);
+            mark[TG_NORMAL64] = k;
+            cudaEventRecord(ev[k++], st);
+            kb_tan1<<<pgrid(b->cnt[wt], b->bsweep[0][1]), 128, 0, st>>>(I, T(wt), b->cnt[wt], d);
+            mark[TG_TAN64] = k;
+            cudaEventRecord(ev[k++], st);
+            kb_flux<<<pgrid(b->cnt[wf], b->bsweep[0][2]), FLUX_BLOCK, FLUX_SMEM, st>>>(I, T(wf), b->cnt[wf], d);
+            mark[TG_FLUX64] = k;
+            cudaEventRecord(ev[k++], st);
+        }
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[k - 1]);
+    for (int g = 0; g < TG_N; g++) {
+        ms[g] = 0.0f;
+        if (e == cudaSuccess && mark[g] > 0) e = cudaEventElapsedTime(&ms[g], ev[mark[g] - 1], ev[mark[g]]);
+    }
+    return e;
+}
+
 extern "C" hgks_status hgks_batch_tune(hgks_batch_t b, double cfl, double *best_ms)
 {
     if (!b || !(cfl > 0.0)) return berr(b, HGKS_ERR_INVALID_ARG, "need cfl > 0");
-    const int n = (int)b->h.size();
-    // snapshot states and control blocks
-    std::vector<double *> saved(n, nullptr);
-    std::vector<Ctl> ctl(n);
     cudaError_t e = cudaStreamSynchronize(b->user);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
-    for (int i = 0; i < n && e == cudaSuccess; i++) {
-        size_t bytes = (size_t)b->inst[i].P.cs * 5 * sizeof(double);
-        e = cudaMalloc(&saved[i], 2 * bytes);
-        if (e == cudaSuccess) e = cudaMemcpy(saved[i], b->h[i]->q[0], bytes, cudaMemcpyDeviceToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(saved[i] + bytes / sizeof(double), b->h[i]->q[1], bytes, cudaMemcpyDeviceToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(&ctl[i], b->h[i]->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost);
+    constexpr int NEV = 8;
+    cudaEvent_t ev[NEV] = {};
+    for (int i = 0; i < NEV && e == cudaSuccess; i++) e = cudaEventCreate(&ev[i]);
+    long long old[WL_N];
+    for (int w = 0; w < WL_N; w++) old[w] = b->tile[w];
+    const long long sweep_cand[] = { 256, 1024, 4096, 16384 }, cell_cand[] = { 2048, 8192, 32768 };
+    std::vector<int> lists;
+    double total = 0.0;
+    for (int g = 0; g < TG_N && e == cudaSuccess; g++) {
+        tg_lists(g, lists);
+        bool present = false;
+        for (int w : lists) present = present || (w != WL_PAD && b->cnt[w] > 0);
+        if (!present) continue;
+        const long long *cand = g == TG_CELLS ? cell_cand : sweep_cand;
+        const int nc = g == TG_CELLS ? 3 : 4;
+        long long best_t = b->tile[lists[0]];
+        float best = 3e38f;
+        for (int c = 0; c < nc && e == cudaSuccess; c++) {
+            for (int w : lists) b->tile[w] = cand[c];
+            if (build_tiles(b) != HGKS_OK) {
+                e = cudaErrorUnknown;
+                break;
+            }
+            float ms[TG_N];
+            e = time_groups(b, ev, ms);  // warm-up
+            if (e == cudaSuccess) e = time_groups(b, ev, ms);
+            if (e == cudaSuccess && ms[g] < best) {
+                best = ms[g];
+                best_t = cand[c];
+            }
+        }
+        for (int w : lists) b->tile[w] = best_t;
+        total += best;
     }
-    auto restore = [&]() {
-        cudaError_t r = cudaStreamSynchronize(b->st);
-        for (int i = 0; i < n && r == cudaSuccess; i++) {
-            size_t bytes = (size_t)b->inst[i].P.cs * 5 * sizeof(double);
-            r = cudaMemcpy(b->h[i]->q[0], saved[i], bytes, cudaMemcpyDeviceToDevice);
-            if (r == cudaSuccess) r = cudaMemcpy(b->h[i]->q[1], saved[i] + bytes / sizeof(double), bytes, cudaMemcpyDeviceToDevice);
-            if (r == cudaSuccess) r = cudaMemcpy(b->h[i]->ctl, &ctl[i], sizeof(Ctl), cudaMemcpyHostToDevice);
-            b->h[i]->cur = ctl[i].good;
-        }
-        return r;
-    };
-    const long long cand[] = { 256, 1024, 4096, 16384 };
-    double best = 1e300;
-    const long long old_ts = b->tile_sweep;
-    long long best_ts = b->tile_sweep;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (e == cudaSuccess) e = cudaEventCreate(&e0);
-    if (e == cudaSuccess) e = cudaEventCreate(&e1);
-    for (long long ts : cand) {
-        if (e != cudaSuccess) break;
-        b->tile_sweep = ts;
-        if (build_tiles(b) != HGKS_OK || capture(b, cfl) != HGKS_OK) {
-            e = cudaErrorUnknown;
-            break;
-        }
-        cudaGraphLaunch(b->exec, b->st);  // warm-up
-        cudaEventRecord(e0, b->st);
-        cudaGraphLaunch(b->exec, b->st);
-        cudaEventRecord(e1, b->st);
-        e = cudaEventSynchronize(e1);
-        float ms = 0.0f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-        if (e == cudaSuccess && ms < best) {
-            best = ms;
-            best_ts = ts;
-        }
-        if (e == cudaSuccess) e = restore();
-    }
-    if (e0) cudaEventDestroy(e0);
-    if (e1) cudaEventDestroy(e1);
-    cudaError_t r = restore();
-    for (int i = 0; i < n; i++)
-        if (saved[i]) cudaFree(saved[i]);
-    if (e != cudaSuccess || r != cudaSuccess) {
-        const std::string msg = std::string("tuning: ") + cudaGetErrorString(e != cudaSuccess ? e : r);
-        b->tile_sweep = old_ts;  // back to the tiling the batch had
+    for (int i = 0; i < NEV; i++)
+        if (ev[i]) cudaEventDestroy(ev[i]);
+    if (e != cudaSuccess) {
+        const std::string msg = std::string("tuning: ") + cudaGetErrorString(e);
+        for (int w = 0; w < WL_N; w++) b->tile[w] = old[w];  // back to the tiling the batch had
         build_tiles(b);
         return berr(b, HGKS_ERR_CUDA, msg);
     }
-    b->tile_sweep = best_ts;
     hgks_status s = build_tiles(b);
     if (s) return s;
-    if (best_ms) *best_ms = best;
+    if (best_ms) *best_ms = total;
     return HGKS_OK;
 }

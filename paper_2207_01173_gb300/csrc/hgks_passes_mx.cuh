@@ -29,6 +29,7 @@
 // face flux is converted to FP64 for the update.
 #pragma once
 #include "hgks_bodies.cuh"
+#include "hgks_f32x2.cuh"
 #include "hgks_ff.cuh"
 #include "hgks_kernels.cuh"
 
@@ -108,10 +109,12 @@ static __host__ __device__ __forceinline__ float ff_dev(float hj, float lj, floa
 struct MxGas {
     float gm1, gm1_lo, K, prc, mu_ref, inv_Tref, omega;
     int power_law;
+    double mu_ref_d, inv_Tref_d, omega_d;  // the viscosity law in FP64 (HGKS_MIXED_T64)
 };
 static __host__ __device__ __forceinline__ MxGas mx_gas(const Params &P)
 {
-    return MxGas{ P.f_gm1, P.f_gm1_lo, P.f_K, P.f_prc, P.f_mu_ref, P.f_inv_Tref, P.f_omega, P.visc_kind == 1 };
+    return MxGas{ P.f_gm1,     P.f_gm1_lo,         P.f_K,          P.f_prc,   P.f_mu_ref, P.f_inv_Tref,
+                  P.f_omega,   P.visc_kind == 1,   P.mu_ref,       1.0 / P.T_ref, P.omega };
 }
 
 // FP32 viscosity law
@@ -257,9 +260,14 @@ static __host__ __device__ __forceinline__ void gp_slopes(const float *col, int 
     }
 }
 
+// T64 = true (HGKS_MIXED_T64): the Maxwellian temperature T0 = p0 / rho0 of the
+// Gauss point, its collision time tau = mu(T0) / p0 and the time-integration
+// coefficients of both windows (dt, dt/2) are formed in FP64 from the
+// float-float Q0 (dtd: the time step in FP64); the sums they weight stay FP32.
+template <bool T64 = false>
 static __host__ __device__ __forceinline__ void gks_point_flux_mixed(const float *col, int st, int n, float ihn,
                                                                   float ih1, float ih2, const MxGas G, float dtf,
-                                                                  ff Fn[5], float dFn[5])
+                                                                  ff Fn[5], float dFn[5], double dtd = 0.0)
 {
     const float gm1 = G.gm1, K = G.K;
     ff Ql[5], Qr[5];
@@ -309,9 +317,87 @@ static __host__ __device__ __forceinline__ void gks_point_flux_mixed(const float
 #pragma unroll
     for (int c = 0; c < 5; c++) q0f[c] = ff_to_float(Q0[c]);
     const Gas<float> g0 = gas_of(q0f, gm1);
-    const float p0f = ff_to_float(p0);
-    const float T0 = p0f * ff_to_float(ir0);
-    const float tau = viscosity_f(G, T0) / p0f;
+    // time-integration coefficients q1..q5 of the windows dt (pass 0) and
+    // dt/2 (pass 1): q1 = tau (2 tau (1 - e) - d - d e), q2 = d^2/2 - tau d +
+    // tau^2 (1 - e), q3 = tau (1 - e), q4 = tau (2 tau (1 - e) - d e),
+    // q5 = tau q3, with e = exp(-d / tau)
+    float qc[2][5];
+    if (T64) {
+        const double p0d = ff_to_double(p0), T0d = p0d / ff_to_double(Q0[0]);
+        const double mud = G.power_law ? G.mu_ref_d * pow(T0d * G.inv_Tref_d, G.omega_d) : G.mu_ref_d;
+        const double taud = mud / p0d;
+        const double ehd = taud > 0.0 ? exp(-0.5 * dtd / taud) : 0.0;
+#pragma unroll
+        for (int pass = 0; pass < 2; pass++) {
+            const double dd = pass == 0 ? dtd : 0.5 * dtd;
+            const double e = pass == 0 ? ehd * ehd : ehd;
+            const double om = 1.0 - e;
+            qc[pass][0] = (float)(taud * (2.0 * taud * om - dd - dd * e));
+            qc[pass][1] = (float)(0.5 * dd * dd - taud * dd + taud * taud * om);
+            qc[pass][2] = (float)(taud * om);
+            qc[pass][3] = (float)(taud * (2.0 * taud * om - dd * e));
+            qc[pass][4] = (float)(taud * taud * om);
+        }
+    } else {
+        const float p0f = ff_to_float(p0);
+        const float T0 = p0f * ff_to_float(ir0);
+        const float tau = viscosity_f(G, T0) / p0f;
+        const float eh = tau > 0.0f ? expf(-0.5f * dtf / tau) : 0.0f;
+#pragma unroll
+        for (int pass = 0; pass < 2; pass++) {
+            const float dd = pass == 0 ? dtf : 0.5f * dtf;
+            const float x = dd / tau;  // +inf for tau = 0
+            if (x < 1.0f) {
+                // a window shorter than the collision time: in q1 = tau^2 f1(x)
+                // and q2 = tau^2 f2(x) the closed forms cancel to O(x^3) and
+                // lose ~2 log10(1/x) digits in FP32, so they are summed as
+                // their Taylor series, f1 = sum_k>=3 (-1)^(k+1) (2 - k) x^k / k!,
+                // f2 = sum_k>=3 (-1)^(k+1) x^k / k! (k <= 13: below 1e-9 of the
+                // first term at x = 1), and 1 - e as -expm1(-x)
+                const float om = -expm1f(-x);
+                const float f1 =
+                    x * x * x *
+                    (-1.0f / 6.0f +
+                     x * (1.0f / 12.0f +
+                          x * (-1.0f / 40.0f +
+                               x * (1.0f / 180.0f +
+                                    x * (-1.0f / 1008.0f +
+                                         x * (1.0f / 6720.0f +
+                                              x * (-1.0f / 51840.0f +
+                                                   x * (1.0f / 453600.0f +
+                                                        x * (-1.0f / 4435200.0f +
+                                                             x * (1.0f / 47900160.0f +
+                                                                  x * (-11.0f / 6227020800.0f)))))))))));
+                const float f2 =
+                    x * x * x *
+                    (1.0f / 6.0f +
+                     x * (-1.0f / 24.0f +
+                          x * (1.0f / 120.0f +
+                               x * (-1.0f / 720.0f +
+                                    x * (1.0f / 5040.0f +
+                                         x * (-1.0f / 40320.0f +
+                                              x * (1.0f / 362880.0f +
+                                                   x * (-1.0f / 3628800.0f +
+                                                        x * (1.0f / 39916800.0f +
+                                                             x * (-1.0f / 479001600.0f +
+                                                                  x * (1.0f / 6227020800.0f)))))))))));
+                const float t2 = tau * tau;
+                qc[pass][0] = t2 * f1;
+                qc[pass][1] = t2 * f2;
+                qc[pass][2] = tau * om;
+                qc[pass][3] = t2 * (2.0f * om - x * (1.0f - om));
+                qc[pass][4] = tau * qc[pass][2];
+            } else {
+                const float e = pass == 0 ? eh * eh : eh;
+                const float om = 1.0f - e;
+                qc[pass][0] = tau * (2.0f * tau * om - dd - dd * e);
+                qc[pass][1] = 0.5f * dd * dd - tau * dd + tau * tau * om;
+                qc[pass][2] = tau * om;
+                qc[pass][3] = tau * (2.0f * tau * om - dd * e);
+                qc[pass][4] = tau * qc[pass][2];
+            }
+        }
+    }
     float B2[5], B3[5], R0[5], B4m1[5], W5[5], B5[5], W6[5], B6[5];
     {
         float s[5], d0[3][5];
@@ -356,18 +442,10 @@ static __host__ __device__ __forceinline__ void gks_point_flux_mixed(const float
     const float h2 = heat_of_g(B2, R0, g0), h3 = heat_of_g(B3, W3, g0), h4 = heat_of_g(b4s, q0f, g0),
                 h5 = heat_of_g(B5, W5, g0), h6 = heat_of_g(B6, W6, g0);
     const float prc = G.prc;
-    const float eh = tau > 0.0f ? expf(-0.5f * dtf / tau) : 0.0f;
     float S[2][5];
 #pragma unroll
     for (int pass = 0; pass < 2; pass++) {
-        const float dd = pass == 0 ? dtf : 0.5f * dtf;
-        const float e = pass == 0 ? eh * eh : eh;
-        const float om = 1.0f - e;
-        const float q1 = tau * (2.0f * tau * om - dd - dd * e);
-        const float q2 = 0.5f * dd * dd - tau * dd + tau * tau * om;
-        const float q3 = tau * om;
-        const float q4 = tau * (2.0f * tau * om - dd * e);
-        const float q5 = tau * q3;
+        const float q1 = qc[pass][0], q2 = qc[pass][1], q3 = qc[pass][2], q4 = qc[pass][3], q5 = qc[pass][4];
 #pragma unroll
         for (int i = 0; i < 5; i++)
             S[pass][i] = q1 * B2[i] + q2 * B3[i] + q3 * B4m1[i] - q4 * B5[i] - q5 * B6[i];
@@ -531,12 +609,15 @@ static __device__ __forceinline__ float inv_metric_f(const Params &P, int e, con
 // that no lane idles at the end of an x row.  The four e2 positions of a tile
 // share the eight t1 rows b0-2 .. b0+5 of every row type, so the block stages
 // those in shared memory once (8 instead of 20 row loads per 4 faces) and
-// prefetches the next row type with cp.async while it reduces the current
-// one; each lane stages its own column.
+// prefetches the next row types with cp.async while it reduces the current
+// ones; each lane stages its own column.  A stage holds two row types
+// interleaved, [array][row][x][type], so that one 8-byte shared load gives a
+// thread the pair of values it reduces together with the packed FP32
+// instructions (hgks_f32x2.cuh).
 // ---------------------------------------------------------------------------
 constexpr int FT_X = 32, FT_B = 4, FT_ROWS = FT_B + 4;
 constexpr int FT_TYPE = 2 * FT_ROWS * FT_X;     // floats of one row type: [array][row][x]
-constexpr int FT_STAGE = 2 * 2 * FT_TYPE;       // [buffer][two row types]
+constexpr int FT_STAGE = 2 * 2 * FT_TYPE;       // [buffer][array][row][x][two row types]
 constexpr int FLUX_MX_TILE_SMEM = FLUX_MX_SMEM + FT_STAGE * (int)sizeof(float);
 
 struct FluxTiling {
@@ -582,6 +663,7 @@ static __device__ __forceinline__ void ft_planes(const T1Mx &in, long long nt, i
 }
 
 // sm: GP_SLOTS floats per thread (Gauss-point inputs), then FT_STAGE floats
+template <bool T64>
 static __device__ __forceinline__ void flux_mx_tile(const Params &P, int d, const Box &Bf, const Box &Bt, T1Mx in,
                                                     double *__restrict__ F, double dt, long long T, float *sm)
 {
@@ -605,12 +687,12 @@ static __device__ __forceinline__ void flux_mx_tile(const Params &P, int d, cons
     const long long base_l = blin(Bt, q0), s2 = bstride(Bt, e2);
     const int rlim = P.n[e2] + 3 - b0;  // rows r with e2 index b0 - 2 + r <= n + 1
     float *gp = sm, *stage = sm + GP_SLOTS * FLUX_MX_BLOCK;
-    const int st = blockDim.x;
+    constexpr int st = FLUX_MX_BLOCK;  // every launch uses this block size: slot offsets become immediates
     float *col = gp + threadIdx.x;
 
     // cooperative staging: thread (lane, wb) copies rows wb, wb + 4 of both
     // arrays for its lane's column (segments wb + 4 i, i = 0..3); a stage
-    // holds two row types
+    // holds two row types u = 0, 1, interleaved
     auto issue = [&](int pair) {
         float *buf = stage + (pair & 1) * (2 * FT_TYPE);
 #pragma unroll
@@ -621,7 +703,7 @@ static __device__ __forceinline__ void flux_mx_tile(const Params &P, int d, cons
             for (int i = 0; i < FT_TYPE / FLUX_MX_BLOCK; i++) {
                 const int seg = wb + 4 * i, arr = seg / FT_ROWS, r = seg % FT_ROWS;
                 if (col_ok && r <= rlim)
-                    cp_async4(buf + u * FT_TYPE + seg * FT_X + lane, (arr ? B : A) + base_l + r * s2);
+                    cp_async4(buf + (seg * FT_X + lane) * 2 + u, (arr ? B : A) + base_l + r * s2);
             }
         }
         cp_async_commit();
@@ -637,45 +719,75 @@ static __device__ __forceinline__ void flux_mx_tile(const Params &P, int d, cons
         Fs[c] = ff{ 0.0f, 0.0f };
         dFs[c] = 0.0f;
     }
-    // reduce the staged rows of row type it into this thread's Gauss-point inputs
-    auto reduce = [&](const float *buf, int it) {
-        const int k = it % 40;
-        float X[5], Y[5];
+    // both row types of a stage at once (it0 even), two lanes per packed
+    // instruction.  Kinds by k = it % 40: 0..9 float-float WENO values,
+    // 10..24 quartic derivatives of float-float values, 25..39 WENO slopes
+    // with quartic values; the pair (24, 25) mixes the last two kinds, so it
+    // runs both and each lane keeps its own kind's results.
+    auto reduce2 = [&](const float *buf, int it0) {
+        const int k = it0 % 40;
+        f2 X[5], Y[5];
 #pragma unroll
         for (int j = 0; j < 5; j++) {
-            X[j] = buf[(0 * FT_ROWS + wb + j) * FT_X + lane];
-            Y[j] = buf[(1 * FT_ROWS + wb + j) * FT_X + lane];
+            X[j] = f2_load(buf + ((0 * FT_ROWS + wb + j) * FT_X + lane) * 2);
+            Y[j] = f2_load(buf + ((1 * FT_ROWS + wb + j) * FT_X + lane) * 2);
         }
-        if (k < 25) {  // float-float values: deviations about the centre row
-            float x[5];
+        float a0, a1, b0, b1;
+        if (k < 10) {  // float-float values: deviations about the centre row
+            f2 x[5];
 #pragma unroll
-            for (int j = 0; j < 5; j++) x[j] = ff_dev(X[j], Y[j], X[2], Y[2]);
-            if (k < 10) {
-                WenoPrep<float> W;
-                weno_prep(x, W);
-                float vm, vp;
-                weno_gauss_pair(W, vm, vp);
-                const ff g0 = ff_add_f(ff{ X[2], Y[2] }, vm), g1 = ff_add_f(ff{ X[2], Y[2] }, vp);
-                col[GP_VAL(0, k, 0) * st] = g0.hi;
-                col[GP_VAL(0, k, 1) * st] = g0.lo;
-                col[GP_VAL(1, k, 0) * st] = g1.hi;
-                col[GP_VAL(1, k, 1) * st] = g1.lo;
-            } else {
-                float dm, dp;
-                quartic_deriv_pair(x, dm, dp);
-                col[GP_S2(0, k - 10) * st] = dm;
-                col[GP_S2(1, k - 10) * st] = dp;
+            for (int j = 0; j < 5; j++) x[j] = f2_ff_dev(X[j], Y[j], X[2], Y[2]);
+            f2 vm, vp, h, l;
+            f2_weno_gauss(x, vm, vp);
+            f2_ff_add_f(X[2], Y[2], vm, h, l);
+            f2_unpack(h, a0, a1);
+            f2_unpack(l, b0, b1);
+            col[GP_VAL(0, k, 0) * st] = a0;
+            col[GP_VAL(0, k + 1, 0) * st] = a1;
+            col[GP_VAL(0, k, 1) * st] = b0;
+            col[GP_VAL(0, k + 1, 1) * st] = b1;
+            f2_ff_add_f(X[2], Y[2], vp, h, l);
+            f2_unpack(h, a0, a1);
+            f2_unpack(l, b0, b1);
+            col[GP_VAL(1, k, 0) * st] = a0;
+            col[GP_VAL(1, k + 1, 0) * st] = a1;
+            col[GP_VAL(1, k, 1) * st] = b0;
+            col[GP_VAL(1, k + 1, 1) * st] = b1;
+            return;
+        }
+        if (k < 25) {  // derivatives along e2 of float-float values (quartic)
+            f2 x[5], dm, dp;
+#pragma unroll
+            for (int j = 0; j < 5; j++) x[j] = f2_ff_dev(X[j], Y[j], X[2], Y[2]);
+            f2_quartic_deriv(x, dm, dp);
+            f2_unpack(dm, a0, a1);
+            f2_unpack(dp, b0, b1);
+            col[GP_S2(0, k - 10) * st] = a0;
+            col[GP_S2(1, k - 10) * st] = b0;
+            if (k + 1 < 25) {
+                col[GP_S2(0, k - 9) * st] = a1;
+                col[GP_S2(1, k - 9) * st] = b1;
             }
-        } else {  // normal slopes (WENO) and first-direction derivatives (quartic value)
-            WenoPrep<float> W;
-            weno_prep(X, W);
-            float s0, s1, q0v, q1v;
-            weno_gauss_pair(W, s0, s1);
-            quartic_value_pair(Y, q0v, q1v);
-            col[GP_SN(0, k - 25) * st] = s0;
-            col[GP_SN(1, k - 25) * st] = s1;
-            col[GP_S1(0, k - 25) * st] = q0v;
-            col[GP_S1(1, k - 25) * st] = q1v;
+        }
+        if (k + 1 >= 25) {  // normal slopes (WENO) and first-direction derivatives (quartic value)
+            f2 s0, s1, q0v, q1v;
+            f2_weno_gauss(X, s0, s1);
+            f2_quartic_value(Y, q0v, q1v);
+            f2_unpack(s0, a0, a1);
+            f2_unpack(s1, b0, b1);
+            float c0, c1, e0, e1;
+            f2_unpack(q0v, c0, c1);
+            f2_unpack(q1v, e0, e1);
+            if (k >= 25) {
+                col[GP_SN(0, k - 25) * st] = a0;
+                col[GP_SN(1, k - 25) * st] = b0;
+                col[GP_S1(0, k - 25) * st] = c0;
+                col[GP_S1(1, k - 25) * st] = e0;
+            }
+            col[GP_SN(0, k - 24) * st] = a1;
+            col[GP_SN(1, k - 24) * st] = b1;
+            col[GP_S1(0, k - 24) * st] = c1;
+            col[GP_S1(1, k - 24) * st] = e1;
         }
     };
     issue(0);
@@ -690,8 +802,7 @@ static __device__ __forceinline__ void flux_mx_tile(const Params &P, int d, cons
         __syncthreads();
         const float *buf = stage + (pair & 1) * (2 * FT_TYPE);
         if (valid) {
-            reduce(buf, 2 * pair);
-            reduce(buf + FT_TYPE, 2 * pair + 1);
+            reduce2(buf, 2 * pair);
             if (pair % 20 == 19) {  // all inputs of line m: the two Gauss-point fluxes
                 const int m = pair / 20;
                 const float ih1 = inv_metric_f(P, e1, P.my_gp, 2 * p[e1] + m);
@@ -700,7 +811,7 @@ static __device__ __forceinline__ void flux_mx_tile(const Params &P, int d, cons
                     const float ih2 = inv_metric_f(P, e2, P.my_gp, 2 * p[e2] + n);
                     ff Fn[5];
                     float dFn[5];
-                    gks_point_flux_mixed(col, st, n, ihn, ih1, ih2, G, dtf, Fn, dFn);
+                    gks_point_flux_mixed<T64>(col, st, n, ihn, ih1, ih2, G, dtf, Fn, dFn, dt);
 #pragma unroll
                     for (int c = 0; c < 5; c++) {
                         Fs[c] = ff_add(Fs[c], ff_scale(Fn[c], 0.25f));  // Gauss weights 1/4 (exact)

@@ -17,7 +17,7 @@ HGKS_OK, HGKS_ERR_INVALID_ARG, HGKS_ERR_OOM, HGKS_ERR_CUDA, HGKS_ERR_NONFINITE, 
 BC_PERIODIC, BC_WALL, BC_EXTERNAL = 0, 1, 2
 STATE_CURRENT, STATE_STAGE = 0, 1
 VISC_CONSTANT, VISC_POWER = 0, 1
-FP64, MIXED = 0, 1
+FP64, MIXED, MIXED_T64 = 0, 1, 2
 
 _STATUS_NAMES = {0: "HGKS_OK", 1: "HGKS_ERR_INVALID_ARG", 2: "HGKS_ERR_OOM", 3: "HGKS_ERR_CUDA",
                  4: "HGKS_ERR_NONFINITE", 5: "HGKS_ERR_TIMEOUT", 6: "HGKS_ERR_STATE"}
@@ -78,7 +78,8 @@ class FlopModel(C.Structure):
 class BatchInfo(C.Structure):
     _fields_ = [("problems", C.c_int), ("tile_sweep", C.c_int), ("tile_cells", C.c_int),
                 ("launches_per_step", C.c_int), ("tiles", C.c_longlong), ("last_ms", C.c_double),
-                ("last_steps", C.c_int)]
+                ("last_steps", C.c_int), ("tile_normal", C.c_int), ("tile_tan1", C.c_int),
+                ("tile_normal_mx", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -378,7 +379,8 @@ class Batch:
         self._check(lib().hgks_batch_step(self.b, nsteps, cfl))
 
     def tune(self, cfl=0.5):
-        """Pick the sweep tile size by timing graph steps; returns the best step time in ms."""
+        """Pick the tile size of each tunable pass by timing it; returns the
+        summed time (ms) of the tuned passes in one timing run."""
         ms = C.c_double()
         self._check(lib().hgks_batch_tune(self.b, cfl, C.byref(ms)))
         return ms.value

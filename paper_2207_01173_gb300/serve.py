@@ -40,6 +40,12 @@ class CudaEngine:
         self.batch = None
         self.members = ()
         self.rebuilds = 0
+        # host seconds spent rebuilding batches: creating them (work-lists on
+        # the device) and, in the first step after each rebuild, capturing and
+        # instantiating the step graph (that call's wall time minus its
+        # device time)
+        self.rebuild_create_s = 0.0
+        self.rebuild_capture_s = 0.0
 
     def footprint(self, req):
         return hgks.footprint_bytes(req["n"], self.precision)
@@ -68,16 +74,23 @@ class CudaEngine:
     def step(self, handles, nsteps):
         """Advance all handles nsteps; returns the step counters after."""
         try:
-            if tuple(handles) != self.members:
+            rebuilt = tuple(handles) != self.members
+            if rebuilt:
                 self._drop_batch()
+                t0 = time.perf_counter()
                 self.batch = hgks.Batch(handles)
+                self.rebuild_create_s += time.perf_counter() - t0
                 self.members = tuple(handles)
                 self.rebuilds += 1
+            t1 = time.perf_counter()
             try:
                 self.batch.step(nsteps, self.cfl)
             except hgks.HgksError as e:
                 if e.status != hgks.HGKS_ERR_NONFINITE:
                     raise
+            if rebuilt:
+                wall = time.perf_counter() - t1
+                self.rebuild_capture_s += max(0.0, wall - self.batch.info()["last_ms"] * 1e-3)
             return self.batch.steps()
         except hgks.HgksError as e:
             self._drop_batch()

@@ -52,9 +52,11 @@ void kh_reconstruct(int n, const double *X, double *weno, double *quartic)
 // the mixed-precision Gauss-point flux: per case Ql, Qr as float-float
 // pairs (hi, lo) [5], slopes dl, dr, d0 [3][5] in FP32 (physical units);
 // outputs F^n (float-float, returned as hi + lo in FP64) and dF^n/dt (FP32)
+// (t64 != 0: the HGKS_MIXED_T64 variant, FP64 temperature, collision time
+// and time coefficients)
 void kh_point_flux_mixed(int n, const float *Ql_hi, const float *Ql_lo, const float *Qr_hi, const float *Qr_lo,
                          const float *dl, const float *dr, const float *d0, double gamma, double Pr, int visc_kind,
-                         double mu_ref, double T_ref, double omega, double dt, double *Fn, double *dFn)
+                         double mu_ref, double T_ref, double omega, double dt, double *Fn, double *dFn, int t64)
 {
     hgks::Params P{};
     P.gamma = gamma;
@@ -89,7 +91,8 @@ void kh_point_flux_mixed(int n, const float *Ql_hi, const float *Ql_lo, const fl
             }
         hgks::ff F[5];
         float dF[5];
-        hgks::gks_point_flux_mixed(col, 1, 0, 1.0f, 1.0f, 1.0f, G, (float)dt, F, dF);
+        if (t64) hgks::gks_point_flux_mixed<true>(col, 1, 0, 1.0f, 1.0f, 1.0f, G, (float)dt, F, dF, dt);
+        else hgks::gks_point_flux_mixed<false>(col, 1, 0, 1.0f, 1.0f, 1.0f, G, (float)dt, F, dF, dt);
         for (int c = 0; c < 5; c++) {
             Fn[5 * i + c] = hgks::ff_to_double(F[c]);
             dFn[5 * i + c] = dF[c];

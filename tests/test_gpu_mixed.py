@@ -28,9 +28,10 @@ def hg():
     return hgks
 
 
-def test_mixed_tgv32_against_oracle(hg, oracle):
+@pytest.mark.parametrize("precision", [1, 2], ids=["mixed", "mixed_t64"])
+def test_mixed_tgv32_against_oracle(hg, oracle, precision):
     n = (32, 32, 32)
-    g = hg.Solver(n, precision=hg.MIXED, **TGV_KW)
+    g = hg.Solver(n, precision=precision, **TGV_KW)
     c = oracle.RefSolver(n, **TGV_KW)
     g.init_tgv(0.1, 1.0, 1.0)
     c.init_tgv(0.1, 1.0, 1.0)
@@ -45,9 +46,10 @@ def test_mixed_tgv32_against_oracle(hg, oracle):
     assert sg["energy"] == pytest.approx(sc["energy"], rel=1e-13)
 
 
-def test_mixed_channel_against_oracle(hg, oracle):
+@pytest.mark.parametrize("precision", [1, 2], ids=["mixed", "mixed_t64"])
+def test_mixed_channel_against_oracle(hg, oracle, precision):
     n = (16, 24, 12)
-    g = hg.Solver(n, precision=hg.MIXED, **channel_kw())
+    g = hg.Solver(n, precision=precision, **channel_kw())
     c = oracle.RefSolver(n, **channel_kw())
     g.init_channel(0.5, 0.1, 2800)
     c.init_channel(0.5, 0.1, 2800)
@@ -144,3 +146,22 @@ def test_mixed_bad_state_is_reported_and_rolled_back(hg):
         g.step(2, 0.5)
     assert e.value.status == hg.HGKS_ERR_NONFINITE
     assert np.array_equal(g.get_state(), q, equal_nan=True)
+
+
+def test_mixed_t64_is_the_mixed_path_with_fp64_coefficients(hg):
+    """HGKS_MIXED_T64 differs from HGKS_MIXED only in the temperature,
+    collision time and time coefficients of each Gauss point: on the TGV
+    (dt / tau ~ 130, where both coefficient sets are accurate) the two runs
+    agree to FP32 rounding of the small terms; batches refuse the variant."""
+    n = (20, 16, 12)
+    a = hg.Solver(n, precision=hg.MIXED, **TGV_KW)
+    b = hg.Solver(n, precision=hg.MIXED_T64, **TGV_KW)
+    for s in (a, b):
+        s.init_tgv(0.1, 1.0, 1.0)
+        s.step(5, 0.5)
+    qa, qb = a.get_state(), b.get_state()
+    assert not np.array_equal(qa, qb)  # the variant really runs other arithmetic
+    assert rel_err(qb, qa).max() < 1e-7
+    with pytest.raises(hg.HgksError) as e:
+        hg.Batch([b])
+    assert e.value.status == hg.HGKS_ERR_INVALID_ARG

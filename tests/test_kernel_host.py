@@ -46,7 +46,7 @@ def kh(tmp_path_factory):
     L.kh_reconstruct.argtypes = [C.c_int, dp, dp, dp]
     fp = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
     L.kh_point_flux_mixed.argtypes = [C.c_int] + [fp] * 7 + [C.c_double, C.c_double, C.c_int, C.c_double,
-                                                              C.c_double, C.c_double, C.c_double, dp, dp]
+                                                              C.c_double, C.c_double, C.c_double, dp, dp, C.c_int]
     L.kh_compat_mixed.argtypes = [C.c_int, fp, fp, fp, fp, C.c_double, dp]
     from oracle import ref
     L.kh_face_flux.argtypes = [dp, C.POINTER(ref.Grid), C.c_double, C.c_double, C.c_int, C.c_double, C.c_double,
@@ -126,9 +126,10 @@ def _split(x):
     return hi, (x - hi.astype(np.float64)).astype(np.float32)
 
 
+@pytest.mark.parametrize("t64", [0, 1], ids=["mixed", "mixed_t64"])
 @pytest.mark.parametrize("jump", [0.0, 1e-4, 1e-3, 0.5, 1.6])
 @pytest.mark.parametrize("visc", sorted(VISC))
-def test_mixed_point_flux_error(oracle, kh, jump, visc):
+def test_mixed_point_flux_error(oracle, kh, jump, visc, t64):
     """The mixed-precision Gauss-point flux (R-MX) against the FP64 oracle on
     the same inputs: float-float states and FP32 slopes, passed to the oracle
     as the FP64 values they represent.
@@ -138,7 +139,9 @@ def test_mixed_point_flux_error(oracle, kh, jump, visc):
     float-only B1 would be off by ~1e-7).  Otherwise F^n is within 1e-5 of the
     flux scale (FP32 small terms, the FP32 direct compatibility sum at larger
     jumps) and dF^n/dt within 2e-3 of its scale (FP32 throughout, with the
-    cancellation of the time slope of Q0)."""
+    cancellation of the time slope of Q0).  The same bounds hold for the
+    HGKS_MIXED_T64 variant (FP64 temperature, collision time and time
+    coefficients)."""
     rng = np.random.default_rng([int(round(jump * 1e4)), sorted(VISC).index(visc), 7])
     n = 150
     Ql, Qr = _states(rng, n, jump)
@@ -149,7 +152,7 @@ def test_mixed_point_flux_error(oracle, kh, jump, visc):
     kind, mu, Tref, om = VISC[visc]
     dt = 0.01
     Fn, dFn = np.empty((n, 5)), np.empty((n, 5))
-    kh.kh_point_flux_mixed(n, lh, ll, rh, rl, dl, dr, d0, GAMMA, 0.72, kind, mu, Tref, om, dt, Fn, dFn)
+    kh.kh_point_flux_mixed(n, lh, ll, rh, rl, dl, dr, d0, GAMMA, 0.72, kind, mu, Tref, om, dt, Fn, dFn, t64)
     ff_only = visc == "inviscid" and jump <= 1e-4
     for i in range(n):
         ql, qr = lh[i] + ll[i].astype(np.float64), rh[i] + rl[i].astype(np.float64)
@@ -234,3 +237,46 @@ def test_mixed_compatibility_error_by_jump(oracle, kh):
     for jump in (1e-6, 1e-5, 1e-4, 4e-4):  # measured: 0.9e-7 x jump
         assert worst[jump] < 2e-7 * jump + 1e-13, (jump, worst[jump])
     assert worst[3e-3] < 1e-6 and worst[3e-2] < 1e-6  # direct FP32 sum, measured 1.4e-7
+
+
+@pytest.mark.parametrize("x", [100.0, 1.0, 0.01, 1e-3])
+def test_mixed_time_coefficients_fp32_against_fp64(oracle, kh, x):
+    """The time-integration coefficients at dt / tau = x.  Written in closed
+    form, the equilibrium coefficients q1 ~ -dt^3 / (6 tau) and
+    q2 ~ dt^3 / (6 tau) cancel to O(x^3) when x << 1 and lose ~2 log10(1/x)
+    digits in FP32 (measured before the change: F^n 1.4e-4, dF^n/dt 2e-2 of
+    their scales at x = 0.01, against 2.6e-6 and 1.2e-4 with FP64
+    coefficients).  HGKS_MIXED sums their Taylor series for x < 1, so its FP32
+    coefficients cost at most a factor 2.5 in accuracy against the FP64
+    coefficients of HGKS_MIXED_T64 at every x; for x >= 0.01 both stay within
+    the mixed-path bounds against the FP64 oracle.  (At x = 1e-3 the other
+    FP32 terms put dF^n/dt of both variants near 3e-3: the near-free-molecular
+    limit is outside the workloads, whose dt / tau lies between 5 and 130.)"""
+    rng = np.random.default_rng([11, int(-np.log10(x) + 10)])
+    n = 120
+    Ql, Qr = _states(rng, n, 0.05)
+    dl, dr, d0 = (np.ascontiguousarray((0.5 * rng.standard_normal((n, 15))).astype(np.float32)) for _ in range(3))
+    (lh, ll), (rh, rl) = _split(Ql), _split(Qr)
+    dt = 0.01
+    # constant viscosity mu = tau p with p ~ 1: tau ~ dt / x
+    kind, mu, Tref, om = 0, dt / x, 1.0, 0.0
+    out = {}
+    for t64 in (0, 1):
+        Fn, dFn = np.empty((n, 5)), np.empty((n, 5))
+        kh.kh_point_flux_mixed(n, lh, ll, rh, rl, dl, dr, d0, GAMMA, 0.72, kind, mu, Tref, om, dt, Fn, dFn, t64)
+        out[t64] = (Fn, dFn)
+    worst = {0: [0.0, 0.0], 1: [0.0, 0.0]}
+    for i in range(n):
+        ql, qr = lh[i] + ll[i].astype(np.float64), rh[i] + rl[i].astype(np.float64)
+        _, _, F, dF = oracle.point_flux(ql, qr, dl[i].astype(np.float64), dr[i].astype(np.float64),
+                                        d0[i].astype(np.float64), GAMMA, 0.72, (kind, mu, Tref, om), dt)
+        for t64 in (0, 1):
+            worst[t64][0] = max(worst[t64][0], np.abs(out[t64][0][i] - F).max() / np.abs(F).max())
+            worst[t64][1] = max(worst[t64][1], np.abs(out[t64][1][i] - dF).max() / np.abs(dF).max())
+    print("dt/tau = %g: FP32 coefficients F %.2e dF %.2e; FP64 coefficients F %.2e dF %.2e"
+          % (x, worst[0][0], worst[0][1], worst[1][0], worst[1][1]))
+    for j in (0, 1):
+        assert worst[0][j] <= 2.5 * worst[1][j] + 1e-6
+    if x >= 0.01:
+        for t64 in (0, 1):
+            assert worst[t64][0] < 1e-5 and worst[t64][1] < 2e-3
