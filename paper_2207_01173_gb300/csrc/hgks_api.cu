@@ -378,12 +378,14 @@ static void enqueue_sweeps(hgks_t h, const double *q, bool record_wall, StepTime
         mark(T, TK_OTHER);
     }
     for (int d = 0; d < 3; d++) {
-        if (mixed) launch_sweep_mixed(P, d, h->qf, h->fq, h->t1, h->F[d], h->ctl, h->st, 0, t64);
+        int nl = 1;
+        if (mixed) nl = launch_sweep_mixed(P, d, h->qf, h->fq, h->t1, h->F[d], h->ctl, h->st, 0, t64);
         else launch_normal(P, d, q, h->fq, h->ctl, h->st);
-        mark(T, TK_NORMAL);
-        if (mixed) launch_sweep_mixed(P, d, h->qf, h->fq, h->t1, h->F[d], h->ctl, h->st, 1, t64);
+        mark(T, TK_NORMAL, nl);
+        nl = 1;
+        if (mixed) nl = launch_sweep_mixed(P, d, h->qf, h->fq, h->t1, h->F[d], h->ctl, h->st, 1, t64);
         else launch_tan1(P, d, h->fq, h->t1, h->ctl, h->st);
-        mark(T, TK_TAN1);
+        mark(T, TK_TAN1, nl);
         if (mixed) launch_sweep_mixed(P, d, h->qf, h->fq, h->t1, h->F[d], h->ctl, h->st, 2, t64);
         else launch_flux(P, d, h->t1, h->F[d], h->ctl, h->st);
         mark(T, TK_FLUX);

@@ -68,9 +68,11 @@ void launch_wall(const Params &P, const double *Fy, Ctl *ctl, double lxlz, cudaS
 cudaError_t fp64_setup();
 cudaError_t mixed_setup();
 void launch_split_mixed(const Params &P, const double *q, double *qf, const Ctl *ctl, cudaStream_t st);
-// t64: the HGKS_MIXED_T64 flux (FP64 temperature, collision time and time coefficients)
-void launch_sweep_mixed(const Params &P, int d, const double *qf, double *fq, double *t1, double *F, const Ctl *ctl,
-                        cudaStream_t st, int which, bool t64 = false);
+// t64: the HGKS_MIXED_T64 flux (FP64 temperature, collision time and time
+// coefficients).  Returns the kernels launched (0 for the first tangential
+// pass of the y and z sweeps, which the normal pass's fused kernel does).
+int launch_sweep_mixed(const Params &P, int d, const double *qf, double *fq, double *t1, double *F, const Ctl *ctl,
+                       cudaStream_t st, int which, bool t64 = false);
 // stage 1: qs = q + dt/2 L + dt^2/8 dL, r = q + dt L + dt^2/6 dL;  stage 2: qn = r + dt^2/3 dL
 void launch_update(const Params &P, int stage, const double *q, const double *const F[3], double *out_a,
                    double *out_b, Ctl *ctl, cudaStream_t st);

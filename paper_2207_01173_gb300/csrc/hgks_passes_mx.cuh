@@ -462,12 +462,14 @@ static __host__ __device__ __forceinline__ void gks_point_flux_mixed(const float
 // ---------------------------------------------------------------------------
 // pass 1: normal reconstruction from the split state
 // ---------------------------------------------------------------------------
-static __device__ __forceinline__ void pos_normal_mx(const Params &P, int d, const Box &B,
-                                                     const float2 *__restrict__ q2, FqMx o, long long t)
+// the normal reconstruction at interface position p (its pass-1 record goes
+// to ov / ovs at index t, planes S apart)
+static __device__ __forceinline__ void normal_mx_at(const Params &P, int d, const int p[3],
+                                                    const float2 *__restrict__ q2, float2 *__restrict__ ov,
+                                                    float *__restrict__ ovs, long long S, long long t)
 {
-    const long long nq = box_count(B);
-    int p[3];
-    bpos(B, t, p);
+    const long long nq = S;
+    FqMx o{ ov, ovs };
     int c0[3] = { p[0], p[1], p[2] };
     c0[d] = p[d] - 3;
     const long long base = pidx(P, c0[0], c0[1], c0[2]);
@@ -511,27 +513,35 @@ static __device__ __forceinline__ void pos_normal_mx(const Params &P, int d, con
     }
 }
 
+static __device__ __forceinline__ void pos_normal_mx(const Params &P, int d, const Box &B,
+                                                     const float2 *__restrict__ q2, FqMx o, long long t)
+{
+    int p[3];
+    bpos(B, t, p);
+    normal_mx_at(P, d, p, q2, o.v, o.vs, box_count(B), t);
+}
+
 // ---------------------------------------------------------------------------
 // pass 2: first tangential direction
 // ---------------------------------------------------------------------------
 // The row loops are fully unrolled: all rows' loads are in flight together
 // (the pass is latency-bound), and with every index a compile-time constant
 // the pass needs fewer registers than with a rolled loop (80 against 128).
-static __device__ __forceinline__ void tan1_mx_rows(int d, const Box &Bt, const Box &Bq,
-                                                    const float2 *__restrict__ v2, const float *__restrict__ vs,
-                                                    float *__restrict__ th,
-                                                    float *__restrict__ tl, float *__restrict__ ts, long long t)
+// The first tangential reconstruction of one position from pass-1 records
+// v2 / vs (planes Sq apart, the position's record at base, its neighbours
+// along the first tangential direction s1 apart), written to th / tl / ts at
+// index t (planes nt apart).
+static __device__ __forceinline__ void tan1_mx_from(const float2 *__restrict__ v2, const float *__restrict__ vs,
+                                                    long long Sq, long long base, long long s1,
+                                                    float *__restrict__ th, float *__restrict__ tl,
+                                                    float *__restrict__ ts, long long nt, long long t)
 {
-    const long long nt = box_count(Bt);
-    int p[3];
-    bpos(Bt, t, p);
-    const long long base = blin(Bq, p), s1 = bstride(Bq, tdir(d, 0));
     // values: Ql, Qr (WENO + quartic), Q0 (quartic)
 #pragma unroll
     for (int v = 0; v < 3; v++) {
 #pragma unroll
         for (int c = 0; c < 5; c++) {
-            const long long off = (long long)(v * 5 + c) * box_count(Bq) + base;
+            const long long off = (long long)(v * 5 + c) * Sq + base;
             float H[5], L[5], x[5];
 #pragma unroll
             for (int j = 0; j < 5; j++) {
@@ -570,7 +580,7 @@ static __device__ __forceinline__ void tan1_mx_rows(int d, const Box &Bt, const 
     for (int w = 0; w < 3; w++) {
 #pragma unroll
         for (int c = 0; c < 5; c++) {
-            const float *src = vs + (long long)(w * 5 + c) * box_count(Bq) + base;
+            const float *src = vs + (long long)(w * 5 + c) * Sq + base;
             float x[5];
 #pragma unroll
             for (int j = 0; j < 5; j++) x[j] = src[(j - 2) * s1];
@@ -582,6 +592,16 @@ static __device__ __forceinline__ void tan1_mx_rows(int d, const Box &Bt, const 
             ts[(1 * 30 + w * 5 + c) * nt + t] = vp;
         }
     }
+}
+
+static __device__ __forceinline__ void tan1_mx_rows(int d, const Box &Bt, const Box &Bq,
+                                                    const float2 *__restrict__ v2, const float *__restrict__ vs,
+                                                    float *__restrict__ th,
+                                                    float *__restrict__ tl, float *__restrict__ ts, long long t)
+{
+    int p[3];
+    bpos(Bt, t, p);
+    tan1_mx_from(v2, vs, box_count(Bq), blin(Bq, p), bstride(Bq, tdir(d, 0)), th, tl, ts, box_count(Bt), t);
 }
 
 // the input and output planes never overlap: passing them as restricted
