@@ -68,7 +68,10 @@ def test_batch_with_walls_matches_and_tunes(hg, oracle):
     ms = b.tune(0.5)
     assert ms > 0.0
     info = b.info()
+    # one tile size per pass group, each from its candidate set
     assert info["tile_sweep"] in (256, 1024, 4096, 16384)
+    assert info["tile_normal"] in (256, 1024, 4096, 16384) and info["tile_tan1"] in (256, 1024, 4096, 16384)
+    assert info["tile_cells"] in (2048, 8192, 32768)
     # tuning left the states where they were
     assert ch2.stats()["step"] == 0
     b.step(3, 0.5)
