@@ -274,7 +274,8 @@ hgks_status hgks_halo_set(hgks_t h, int state, int dir, int side, const double *
  * Stage 2 reads the device status once (as hgks_step does) and reports a bad
  * state with NONFINITE, leaving the state at the last completed step.
  * Errors: INVALID_ARG (stage not 1 or 2, dt <= 0), STATE (stage 2 without a
- * stage 1 of the same step), NONFINITE, CUDA. */
+ * stage 1 of the same step: a whole step, a state copy in or an initial field
+ * in between also cancels the pending stage 1), NONFINITE, CUDA. */
 hgks_status hgks_stage(hgks_t h, int stage, double dt);
 
 /* Largest grid (cells) accepted by hgks_cfl_dt_noalloc. */

@@ -261,6 +261,7 @@ static hgks_status write_ctl(hgks_t h, const Ctl &c)
 
 static hgks_status reset_clock(hgks_t h)
 {
+    h->stage1_done = false;  // a new state: no stage of a step in progress
     Ctl c;
     hgks_status s = read_ctl(h, c);
     if (s) return s;
@@ -313,6 +314,7 @@ extern "C" hgks_status hgks_init_density_wave(hgks_t h, double amp)
 extern "C" hgks_status hgks_set_state(hgks_t h, const double *host_q)
 {
     if (!h || !host_q) return set_err(h, HGKS_ERR_INVALID_ARG, "null argument");
+    h->stage1_done = false;
     CK(h, cudaMemcpyAsync(h->io[0], host_q, (size_t)h->P.ncell * 5 * sizeof(double), cudaMemcpyHostToDevice, h->st));
     launch_scatter(h->P, h->io[0], h->q[h->cur], h->st);
     CK(h, cudaGetLastError());
@@ -432,6 +434,7 @@ static void enqueue_step(hgks_t h, double cfl, double fixed_dt, StepTimer *T = n
 
 static hgks_status run_steps(hgks_t h, int nsteps, double cfl, double fixed_dt)
 {
+    h->stage1_done = false;  // whole steps overwrite the stage state
     for (int s = 0; s < nsteps; s++) enqueue_step(h, cfl, fixed_dt);
     CK(h, cudaGetLastError());
     Ctl c;

@@ -165,3 +165,23 @@ def test_mixed_t64_is_the_mixed_path_with_fp64_coefficients(hg):
     with pytest.raises(hg.HgksError) as e:
         hg.Batch([b])
     assert e.value.status == hg.HGKS_ERR_INVALID_ARG
+
+
+def test_mixed_long_ragged_x_rows_against_oracle(hg, oracle):
+    """x rows longer than one 128-position segment of the fused y/z-sweep
+    kernel, with a ragged tail (133 = 128 + 5), on a rough state (nonlinear
+    WENO weights everywhere): the mixed path against the FP64 oracle after 3
+    steps.  Its per-cell jumps of a few percent take the direct FP32
+    compatibility branch, so the bound is the noisy channel's (1e-5)."""
+    from tests.inputs import rough_state
+    n = (133, 6, 5)
+    kw = dict(visc=(0, 1e-3, 1.0, 0.0), Pr=0.72)
+    g = hg.Solver(n, precision=hg.MIXED, **kw)
+    c = oracle.RefSolver(n, **kw)
+    q = rough_state(n, 21)
+    g.set_state(q)
+    c.set_state(q)
+    g.step(3, 0.5)
+    c.step(3, 0.5)
+    err = rel_err(g.get_state(), c.get_state())
+    assert err.max() < 1e-5, err

@@ -114,6 +114,19 @@ def test_stage_order_and_batch_rejection(hg):
     with pytest.raises(hg.HgksError) as e:
         sv.stage(2, 1e-3)  # stage 2 before stage 1
     assert e.value.status == hg.HGKS_ERR_STATE
+    # one slab alone is its own periodic neighbour: set its halos, run stage 1
+    lo = torch.empty(sv.halo_count(), dtype=torch.float64, device="cuda")
+    hi = torch.empty_like(lo)
+    sv.fill_ghosts(0)
+    sv.halo_get(0, 0, lo.data_ptr())
+    sv.halo_get(0, 1, hi.data_ptr())
+    sv.halo_set(0, 0, hi.data_ptr())
+    sv.halo_set(0, 1, lo.data_ptr())
+    sv.stage(1, 1e-3)
+    sv.set_state(sv.get_state())  # a new state in between cancels the pending stage 1
+    with pytest.raises(hg.HgksError) as e:
+        sv.stage(2, 1e-3)
+    assert e.value.status == hg.HGKS_ERR_STATE
     with pytest.raises(hg.HgksError) as e:
         sv.halo_get(0, 0, 0)  # NULL buffer
     assert e.value.status == hg.HGKS_ERR_INVALID_ARG

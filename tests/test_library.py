@@ -59,6 +59,10 @@ def test_invalid_arguments_rejected_before_device():
     with pytest.raises(hgks.HgksError) as e:
         hgks.Solver((8, 2, 8), bc_lo=(0, 1, 0), bc_hi=(0, 1, 0))
     assert e.value.status == hgks.HGKS_ERR_INVALID_ARG
+    # an empty grid
+    with pytest.raises(hgks.HgksError) as e:
+        hgks.Solver((0, 8, 8))
+    assert e.value.status == hgks.HGKS_ERR_INVALID_ARG
     # sub-domain sides: z only, and at least three planes
     with pytest.raises(hgks.HgksError) as e:
         hgks.Solver((8, 8, 8), bc_lo=(2, 0, 0), bc_hi=(2, 0, 0))
