@@ -52,8 +52,9 @@ METRIC = "cell-updates/s TGV 256^3 FP64 vs mixed at stated error; serve p50/p99 
 # only twice the L2, a launch moved 1.02 instead of 1.73 kB per face).
 K_FLUX_DRAM_BYTES_PER_FACE = (3341.87e6 + 306.34e6) / 2113536
 K_FLUX_TRAFFIC_CURRENT = True
-# the same for k_flux_mx (2012 MB read + 170 MB written per 128^3 launch)
-K_FLUX_MX_DRAM_BYTES_PER_FACE = (2012.23e6 + 170.33e6) / 2113536
+# the same for k_flux_mx (2010 MB read + 170 MB written per 128^3 launch,
+# mean of 24 launches of the current build)
+K_FLUX_MX_DRAM_BYTES_PER_FACE = (2010.1e6 + 170.2e6) / 2113536
 # GB300 FP32 (non-tensor) peak: 152 SMs x 128 FP32 lanes x 2 flops per FMA x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # Table 3 of the paper: 256^3 TGV, FP64, Tesla V100, 11.697 h for 20 t_c at dt = 8.925e-4

@@ -118,6 +118,38 @@ static __device__ __forceinline__ void f2_weno_gauss(const f2 X[5], f2 &vm, f2 &
     vm = f2_fma(mga, f2_mul(f2_mul(nm, dp), r), X[2]);
 }
 
+// WENO-Z of two stencils (hgks_device.cuh weno_prep + weno_edge_pair): the
+// values at the two cell edges, -1/2 (vl) and +1/2 (vr)
+static __device__ __forceinline__ void f2_weno_edge(const f2 X[5], f2 &vl, f2 &vr)
+{
+    const f2 h = f2_bcast(0.5f), t3 = f2_bcast(1.5f), mh = f2_bcast(-0.5f);
+    const f2 d1 = f2_sub(X[1], X[0]), d2 = f2_sub(X[2], X[1]), d3 = f2_sub(X[3], X[2]), d4 = f2_sub(X[4], X[3]);
+    const f2 c20 = f2_mul(h, f2_sub(d2, d1)), c10 = f2_fma(t3, d2, f2_mul(mh, d1));
+    const f2 c21 = f2_mul(h, f2_sub(d3, d2)), c11 = f2_mul(h, f2_add(d3, d2));
+    const f2 c22 = f2_mul(h, f2_sub(d4, d3)), c12 = f2_fma(t3, d3, f2_mul(mh, d4));
+    const f2 k133 = f2_bcast((float)(13.0 / 3.0)), eps = f2_bcast((float)WENO_EPS);
+    const f2 b0 = f2_fma(c10, c10, f2_fma(f2_mul(k133, c20), c20, eps));
+    const f2 b1 = f2_fma(c11, c11, f2_fma(f2_mul(k133, c21), c21, eps));
+    const f2 b2 = f2_fma(c12, c12, f2_fma(f2_mul(k133, c22), c22, eps));
+    const f2 tau5 = f2_abs(f2_sub(b0, b2));
+    const f2 cw0 = f2_mul(f2_add(b0, tau5), f2_mul(b1, b2));
+    const f2 cw1 = f2_mul(f2_add(b1, tau5), f2_mul(b0, b2));
+    const f2 cw2 = f2_mul(f2_add(b2, tau5), f2_mul(b0, b1));
+    const f2 c01 = f2_bcast(0.1f), c03 = f2_bcast(0.3f), c06 = f2_bcast(0.6f), c16 = f2_bcast((float)(1.0 / 6.0));
+    const f2 a1 = f2_mul(c06, cw1);
+    const f2 r0 = f2_mul(c01, cw0), r2 = f2_mul(c03, cw2);  // right edge weights
+    const f2 l0 = f2_mul(c03, cw0), l2 = f2_mul(c01, cw2);  // left edge weights
+    const f2 p0 = f2_fma(c20, c16, X[2]), p1 = f2_fma(c21, c16, X[2]), p2 = f2_fma(c22, c16, X[2]);
+    const f2 nr = f2_fma(r0, f2_fma(h, c10, p0), f2_fma(a1, f2_fma(h, c11, p1), f2_mul(r2, f2_fma(h, c12, p2))));
+    const f2 nl = f2_fma(l0, f2_fma(mh, c10, p0), f2_fma(a1, f2_fma(mh, c11, p1), f2_mul(l2, f2_fma(mh, c12, p2))));
+    const f2 dr = f2_add(f2_add(r0, a1), r2), dl = f2_add(f2_add(l0, a1), l2);
+    float den_x, den_y;
+    f2_unpack(f2_mul(dr, dl), den_x, den_y);
+    const f2 r = f2_pack(weno_recip<float>(den_x), weno_recip<float>(den_y));
+    vr = f2_mul(f2_mul(nr, dl), r);
+    vl = f2_mul(f2_mul(nl, dr), r);
+}
+
 // quartic through five averages (hgks_device.cuh quartic_value_pair /
 // quartic_deriv_pair): values and derivatives at -+sqrt(3)/6
 static __device__ __forceinline__ void f2_quartic_value(const f2 X[5], f2 &vm, f2 &vp)

@@ -485,25 +485,34 @@ static __device__ __forceinline__ void normal_mx_at(const Params &P, int d, cons
             H[m] = e.x;
             L[m] = e.y;
         }
-        float xl[5], xr[5];
+        // the stencils of cell f-1 (lane x) and cell f (lane y), each as
+        // deviations about its centre, reconstructed together on packed pairs
+        f2 X[5];
+        const f2 Hc = f2_pack(H[2], H[3]), Lc = f2_pack(L[2], L[3]);
 #pragma unroll
-        for (int m = 0; m < 5; m++) {
-            xl[m] = ff_dev(H[m], L[m], H[2], L[2]);          // cell f-1 stencil, about its centre
-            xr[m] = ff_dev(H[m + 1], L[m + 1], H[3], L[3]);  // cell f stencil
-        }
-        WenoPrep<float> wl, wr;
-        weno_prep(xl, wl);
-        weno_prep(xr, wr);
-        float lm_l, lm_r, r_l, r_r;
-        weno_edge_pair(wl, lm_l, lm_r);
-        weno_edge_pair(wr, r_l, r_r);
-        Ql[c] = ff_add_f(ff{ H[2], L[2] }, lm_r);
-        Qr[c] = ff_add_f(ff{ H[3], L[3] }, r_l);
+        for (int m = 0; m < 5; m++) X[m] = f2_ff_dev(f2_pack(H[m], H[m + 1]), f2_pack(L[m], L[m + 1]), Hc, Lc);
+        f2 vl, vr;
+        f2_weno_edge(X, vl, vr);  // (cell f-1, cell f) at their left and right edges
+        float lm_l, r_l, lm_r, r_r;
+        f2_unpack(vl, lm_l, r_l);
+        f2_unpack(vr, lm_r, r_r);
+        // Ql: cell f-1's right edge; Qr: cell f's left edge
+        f2 qh, ql;
+        f2_ff_add_f(Hc, Lc, f2_pack(lm_r, r_l), qh, ql);
+        f2_unpack(qh, Ql[c].hi, Qr[c].hi);
+        f2_unpack(ql, Ql[c].lo, Qr[c].lo);
         o.v[(0 * 5 + c) * nq + t] = make_float2(Ql[c].hi, Ql[c].lo);
         o.v[(1 * 5 + c) * nq + t] = make_float2(Qr[c].hi, Qr[c].lo);
-        o.vs[(0 * 5 + c) * nq + t] = 2.0f * lm_l + 4.0f * lm_r;  // parabola slopes (centre cancels)
-        o.vs[(1 * 5 + c) * nq + t] = -4.0f * r_l - 2.0f * r_r;
-        o.vs[(2 * 5 + c) * nq + t] = (15.0f * xl[3] - (xl[4] - xl[1])) * (1.0f / 12.0f);
+        // parabola slopes (centre cancels): 2 lm_l + 4 lm_r and -4 r_l - 2 r_r
+        float sl, sr;
+        f2_unpack(f2_fma(f2_pack(2.0f, -4.0f), vl, f2_mul(f2_pack(4.0f, -2.0f), vr)), sl, sr);
+        o.vs[(0 * 5 + c) * nq + t] = sl;
+        o.vs[(1 * 5 + c) * nq + t] = sr;
+        float x1, x1r, x3, x3r, x4, x4r;
+        f2_unpack(X[1], x1, x1r);
+        f2_unpack(X[3], x3, x3r);
+        f2_unpack(X[4], x4, x4r);
+        o.vs[(2 * 5 + c) * nq + t] = (15.0f * x3 - (x4 - x1)) * (1.0f / 12.0f);
     }
     ff Q0[5];
     compat_mixed(Ql, Qr, P.f_gm1, P.f_K, Q0);
@@ -536,61 +545,127 @@ static __device__ __forceinline__ void tan1_mx_from(const float2 *__restrict__ v
                                                     float *__restrict__ th, float *__restrict__ tl,
                                                     float *__restrict__ ts, long long nt, long long t)
 {
-    // values: Ql, Qr (WENO + quartic), Q0 (quartic)
+    // Rows are reduced two at a time on packed FP32 pairs (hgks_f32x2.cuh):
+    // the Ql and Qr rows of one component together (WENO + quartic), the Q0
+    // rows of components (0, 1) and (2, 3) (quartic), and the slope rows in
+    // consecutive pairs (WENO); the Q0 row of component 4 and the last slope
+    // row run alone.  Value index k (0..24) of a Gauss point: 0..9 WENO values
+    // of Ql, Qr; 10..24 quartic values of Ql, Qr, Q0.
+    auto put_value = [&](int k, f2 m, f2 p, int step) {  // hi parts of float-float values, both Gauss points
+        float a0, a1, b0, b1;
+        f2_unpack(m, a0, a1);
+        f2_unpack(p, b0, b1);
+        th[(0 * 25 + k) * nt + t] = a0;
+        th[(1 * 25 + k) * nt + t] = b0;
+        th[(0 * 25 + k + step) * nt + t] = a1;
+        th[(1 * 25 + k + step) * nt + t] = b1;
+    };
+    auto put_lo = [&](int k, f2 m, f2 p, int step) {
+        float a0, a1, b0, b1;
+        f2_unpack(m, a0, a1);
+        f2_unpack(p, b0, b1);
+        tl[(0 * 25 + k) * nt + t] = a0;
+        tl[(1 * 25 + k) * nt + t] = b0;
+        tl[(0 * 25 + k + step) * nt + t] = a1;
+        tl[(1 * 25 + k + step) * nt + t] = b1;
+    };
+    auto put_slope = [&](int k, f2 m, f2 p, int step) {  // FP32 slopes / derivatives, index k of 30
+        float a0, a1, b0, b1;
+        f2_unpack(m, a0, a1);
+        f2_unpack(p, b0, b1);
+        ts[(0 * 30 + k) * nt + t] = a0;
+        ts[(1 * 30 + k) * nt + t] = b0;
+        ts[(0 * 30 + k + step) * nt + t] = a1;
+        ts[(1 * 30 + k + step) * nt + t] = b1;
+    };
+    // two value rows (planes r0, r1 of the pass-1 record) as packed (hi, lo)
+    // deviations about their centres
+    auto load_pair = [&](int r0, int r1, f2 H[5], f2 L[5], f2 x[5]) {
+        const long long o0 = (long long)r0 * Sq + base, o1 = (long long)r1 * Sq + base;
 #pragma unroll
-    for (int v = 0; v < 3; v++) {
-#pragma unroll
-        for (int c = 0; c < 5; c++) {
-            const long long off = (long long)(v * 5 + c) * Sq + base;
-            float H[5], L[5], x[5];
-#pragma unroll
-            for (int j = 0; j < 5; j++) {
-                const float2 e = v2[off + (j - 2) * s1];
-                H[j] = e.x;
-                L[j] = e.y;
-            }
-#pragma unroll
-            for (int j = 0; j < 5; j++) x[j] = ff_dev(H[j], L[j], H[2], L[2]);
-            const ff ctr{ H[2], L[2] };
-            if (v < 2) {
-                WenoPrep<float> W;
-                weno_prep(x, W);
-                float vm, vp;
-                weno_gauss_pair(W, vm, vp);
-                const ff am = ff_add_f(ctr, vm), ap = ff_add_f(ctr, vp);
-                th[(0 * 25 + v * 5 + c) * nt + t] = am.hi;
-                tl[(0 * 25 + v * 5 + c) * nt + t] = am.lo;
-                th[(1 * 25 + v * 5 + c) * nt + t] = ap.hi;
-                tl[(1 * 25 + v * 5 + c) * nt + t] = ap.lo;
-            }
-            float qm, qp, dm, dp;
-            quartic_value_pair(x, qm, qp);
-            quartic_deriv_pair(x, dm, dp);
-            const ff bm = ff_add_f(ctr, qm), bp = ff_add_f(ctr, qp);
-            th[(0 * 25 + 10 + v * 5 + c) * nt + t] = bm.hi;
-            tl[(0 * 25 + 10 + v * 5 + c) * nt + t] = bm.lo;
-            th[(1 * 25 + 10 + v * 5 + c) * nt + t] = bp.hi;
-            tl[(1 * 25 + 10 + v * 5 + c) * nt + t] = bp.lo;
-            ts[(0 * 30 + 15 + v * 5 + c) * nt + t] = dm;
-            ts[(1 * 30 + 15 + v * 5 + c) * nt + t] = dp;
+        for (int j = 0; j < 5; j++) {
+            const float2 a = v2[o0 + (j - 2) * s1], b = v2[o1 + (j - 2) * s1];
+            H[j] = f2_pack(a.x, b.x);
+            L[j] = f2_pack(a.y, b.y);
         }
+#pragma unroll
+        for (int j = 0; j < 5; j++) x[j] = f2_ff_dev(H[j], L[j], H[2], L[2]);
+    };
+    // values of Ql and Qr, component c: WENO and quartic values, quartic derivatives
+#pragma unroll
+    for (int c = 0; c < 5; c++) {
+        f2 H[5], L[5], x[5], m, p, rh0, rl0, rh1, rl1;
+        load_pair(c, 5 + c, H, L, x);
+        f2_weno_gauss(x, m, p);
+        f2_ff_add_f(H[2], L[2], m, rh0, rl0);
+        f2_ff_add_f(H[2], L[2], p, rh1, rl1);
+        put_value(c, rh0, rh1, 5);
+        put_lo(c, rl0, rl1, 5);
+        f2_quartic_value(x, m, p);
+        f2_ff_add_f(H[2], L[2], m, rh0, rl0);
+        f2_ff_add_f(H[2], L[2], p, rh1, rl1);
+        put_value(10 + c, rh0, rh1, 5);
+        put_lo(10 + c, rl0, rl1, 5);
+        f2_quartic_deriv(x, m, p);
+        put_slope(15 + c, m, p, 5);
     }
-    // slopes: WENO-Z in FP32
+    // values of Q0, components (0, 1) and (2, 3): quartic values and derivatives
 #pragma unroll
-    for (int w = 0; w < 3; w++) {
+    for (int c = 0; c < 4; c += 2) {
+        f2 H[5], L[5], x[5], m, p, rh0, rl0, rh1, rl1;
+        load_pair(10 + c, 11 + c, H, L, x);
+        f2_quartic_value(x, m, p);
+        f2_ff_add_f(H[2], L[2], m, rh0, rl0);
+        f2_ff_add_f(H[2], L[2], p, rh1, rl1);
+        put_value(20 + c, rh0, rh1, 1);
+        put_lo(20 + c, rl0, rl1, 1);
+        f2_quartic_deriv(x, m, p);
+        put_slope(25 + c, m, p, 1);
+    }
+    {  // Q0, component 4, alone
+        const long long off = (long long)14 * Sq + base;
+        float H[5], L[5], x[5];
 #pragma unroll
-        for (int c = 0; c < 5; c++) {
-            const float *src = vs + (long long)(w * 5 + c) * Sq + base;
-            float x[5];
-#pragma unroll
-            for (int j = 0; j < 5; j++) x[j] = src[(j - 2) * s1];
-            WenoPrep<float> W;
-            weno_prep(x, W);
-            float vm, vp;
-            weno_gauss_pair(W, vm, vp);
-            ts[(0 * 30 + w * 5 + c) * nt + t] = vm;
-            ts[(1 * 30 + w * 5 + c) * nt + t] = vp;
+        for (int j = 0; j < 5; j++) {
+            const float2 e = v2[off + (j - 2) * s1];
+            H[j] = e.x;
+            L[j] = e.y;
         }
+#pragma unroll
+        for (int j = 0; j < 5; j++) x[j] = ff_dev(H[j], L[j], H[2], L[2]);
+        const ff ctr{ H[2], L[2] };
+        float qm, qp, dm, dp;
+        quartic_value_pair(x, qm, qp);
+        quartic_deriv_pair(x, dm, dp);
+        const ff bm = ff_add_f(ctr, qm), bp = ff_add_f(ctr, qp);
+        th[(0 * 25 + 24) * nt + t] = bm.hi;
+        tl[(0 * 25 + 24) * nt + t] = bm.lo;
+        th[(1 * 25 + 24) * nt + t] = bp.hi;
+        tl[(1 * 25 + 24) * nt + t] = bp.lo;
+        ts[(0 * 30 + 29) * nt + t] = dm;
+        ts[(1 * 30 + 29) * nt + t] = dp;
+    }
+    // slopes (15 rows, w * 5 + c): WENO-Z of pairs of rows, the last alone
+#pragma unroll
+    for (int r = 0; r < 14; r += 2) {
+        const float *s0 = vs + (long long)r * Sq + base, *s1p = vs + (long long)(r + 1) * Sq + base;
+        f2 X[5], m, p;
+#pragma unroll
+        for (int j = 0; j < 5; j++) X[j] = f2_pack(s0[(j - 2) * s1], s1p[(j - 2) * s1]);
+        f2_weno_gauss(X, m, p);
+        put_slope(r, m, p, 1);
+    }
+    {
+        const float *src = vs + (long long)14 * Sq + base;
+        float x[5];
+#pragma unroll
+        for (int j = 0; j < 5; j++) x[j] = src[(j - 2) * s1];
+        WenoPrep<float> W;
+        weno_prep(x, W);
+        float vm, vp;
+        weno_gauss_pair(W, vm, vp);
+        ts[(0 * 30 + 14) * nt + t] = vm;
+        ts[(1 * 30 + 14) * nt + t] = vp;
     }
 }
 

@@ -99,7 +99,7 @@ def history_rel(hist, g, keys):
 
 
 # the oracle histories stored under tests/golden/
-HISTORIES = ["channel"]
+HISTORIES = ["tgv64", "channel"]
 
 
 @pytest.mark.parametrize("name", HISTORIES)
@@ -113,7 +113,10 @@ def test_fp64_history_matches_oracle(hg, name):
         assert rel[key] < 1e-6, (key, rel[key])
         assert rel[key] < 1e-9, (key, rel[key])
     assert rel["t"] < 1e-12 and rel["dt"] < 1e-12
-    assert rel["mass"] < 1e-13 and rel["energy"] < 1e-13
+    # totals are sums over every cell taken in different orders (a tree on the
+    # GPU, serial in the oracle): rounding of order sqrt(N) eps, N = 64^3
+    # (measured 2.2e-13)
+    assert rel["mass"] < 1e-12 and rel["energy"] < 1e-12
     for k, e in errs.items():
         print("  sampled cells after %d steps: %s" % (k, e))
         assert e.max() < (1e-11 if k <= 10 else 1e-9), (k, e)
