@@ -7,12 +7,13 @@ CFL 0.5), synthetic data (the exact-average TGV initial field).
 Prints one JSON line (rank 0).  Besides the FP64 headline (`value`, its
 roofline and an end-to-end figure through host buffers) the line carries:
   mixed    - the same workload in mixed precision, with its error against
-             the FP64 run and a roofline against the FP32 pipe;
+             the FP64 run and a roofline against the FP32 pipe, and the
+             HGKS_MIXED_T64 variant's cost and error (t64_variant);
   batched  - 64 Taylor-Green problems on uneven grids, stepped one by one and
-             as one batch (--batch-steps), FP64 and mixed;
-  serve    - the first --serve-requests requests of the seeded 500-request
-             stream through the continuous-batching serve loop;
-  cpu_baseline - the CPU oracle on a bounded sample (TGV 32^3).
+             as one batch (--batch-steps, default 50), FP64 and mixed;
+  serve    - the first --serve-requests (default 100) requests of the seeded
+             500-request stream through the continuous-batching serve loop;
+  cpu_baseline - the CPU oracle on bounded samples (TGV 64^3 and 32^3).
 With N > 1 (torchrun, one process per GPU) every rank advances its own
 independent replica (the slab decomposition is host logic tested on CPU
 ranks; one GPU per run here); value is the total over ranks and the time is
