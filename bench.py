@@ -478,13 +478,22 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        solver.set_state(q_host)
-        solver.step(1, CFL)
-        solver.get_state(out_host)
-    torch.cuda.synchronize()
-    e2e_s = max_over_ranks(time.perf_counter() - t0, device="cuda")
+    phase = {"h2d_ms": 0.0, "step_ms": 0.0, "d2h_ms": 0.0}
+    with ClockSampler(local_rank) as clk_e2e:
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            ta = time.perf_counter()
+            solver.set_state(q_host)
+            tb = time.perf_counter()
+            solver.step(1, CFL)
+            tc = time.perf_counter()
+            solver.get_state(out_host)
+            td = time.perf_counter()
+            phase["h2d_ms"] += (tb - ta) * 1e3 / e2e_steps
+            phase["step_ms"] += (tc - tb) * 1e3 / e2e_steps
+            phase["d2h_ms"] += (td - tc) * 1e3 / e2e_steps
+        torch.cuda.synchronize()
+        e2e_s = max_over_ranks(time.perf_counter() - t0, device="cuda")
     e2e_value = world * cells * e2e_steps / e2e_s
     stats = solver.stats()
 
@@ -528,7 +537,8 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": launches,
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": "cell-updates/s", "h2d_bytes_per_step": 5 * cells * 8,
-                "d2h_bytes_per_step": 5 * cells * 8, "steps": e2e_steps},
+                "d2h_bytes_per_step": 5 * cells * 8, "steps": e2e_steps,
+                "phase_ms_per_step": phase, "clocks": clk_e2e.summary()},
         "cpu_baseline": cpu_baseline,
         "mixed": mixed,
         "batched": batched,
