@@ -24,11 +24,9 @@
  * the paper's Table 3, and tests/test_oracle_mutants.py plants plausible
  * slips one at a time, each of which must fail a pin.  Parity unpinned:
  * agreement with the paper's own implementation, whose code and output the
- * paper does not print beyond Table 3; and two details that no physical pin
- * resolves, the rho factor of the wall ghost's kinetic energy (checked only
- * against the definition of R-BC) and the positivity tests of density and
- * internal energy in the bad-state check (guards that a non-finite value
- * pre-empts).
+ * paper does not print beyond Table 3; and one detail that no physical pin
+ * resolves, the positivity tests of density and internal energy in the
+ * bad-state check (guards that a non-finite value pre-empts).
  */
 #include "hgks_ref.h"
 

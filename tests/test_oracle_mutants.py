@@ -151,6 +151,10 @@ MUTANTS = [
     ("wall_mirror_offset", "else s = side == 0 ? m : n - 1 - m;", "else s = side == 0 ? m + 1 : n - 1 - m;",
      [S + "test_wall_modes_decay"]),
     ("wall_ghost_density", "double rho = p / Tg;", "double rho = W[0];", [S + "test_wall_modes_decay"]),
+    ("wall_ghost_kinetic_energy_interior_density",
+     "dst[4] = p / (h->gas.gamma - 1.0) + 0.5 * rho * (U * U + V * V + Wv * Wv);",
+     "dst[4] = p / (h->gas.gamma - 1.0) + 0.5 * W[0] * (U * U + V * V + Wv * Wv);",
+     [S + "test_wall_ghost_face_conditions"]),
     ("wall_shear_normalisation", "h->wall_shear = walls ? s / (walls * h->g.lx * h->g.lz) : 0.0;",
      "h->wall_shear = walls ? s / (walls * h->g.lx) : 0.0;", [S + "test_channel_wall_shear_laminar"]),
     # S2O4, gas model, kinetic weights

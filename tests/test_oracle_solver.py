@@ -694,6 +694,50 @@ def test_wall_ghost_definition(oracle):
             np.testing.assert_allclose(qg, cons(rg, *(-U), pi), rtol=1e-13)
 
 
+def test_wall_ghost_face_conditions(oracle):
+    """The isothermal no-slip wall (Sec. 4.2: "non-slip and isothermal") as
+    conditions at the wall face, read from the ghost cells' conservative
+    variables through the equation of state alone: the face averages of the
+    velocity of each ghost / interior pair vanish (no slip), the face average
+    of their temperature is T_w (isothermal), and their pressures agree (the
+    wall carries the fluid's pressure, no jump across the face).  Checked on a
+    state with rho != 1, T != T_w and flow at the walls, where the ghost
+    density differs from the interior one, so the ghost's kinetic energy must
+    be formed with the ghost's own density for the pressure to come out
+    equal."""
+    n, Tw = (4, 6, 3), 1.1
+    s = oracle.RefSolver(n, lengths=(1.0, 2.0, 1.0), origin=(0.0, -1.0, 0.0), bc_lo=(0, 1, 0), bc_hi=(0, 1, 0),
+                         T_wall=Tw)
+    rng = np.random.default_rng(5)
+    shape = (n[2], n[1], n[0])
+    rho = 1.6 + 0.3 * rng.uniform(-1, 1, shape)
+    vel = 0.5 * rng.uniform(-1, 1, (3,) + shape)
+    p = 1.2 + 0.2 * rng.uniform(-1, 1, shape)
+    s.set_state(cons(rho, *vel, p))
+    seen = []
+    s.set_hooks(halo=lambda q: seen.append(q.copy()))
+    s.stats()  # one ghost fill
+    q = seen[-1]
+    NG = oracle.NG
+
+    def prim(c):
+        r = c[0]
+        U = c[1:4] / r
+        pr = (GAMMA - 1) * (c[4] - 0.5 * r * (U ** 2).sum(0))
+        return r, U, pr, pr / r
+
+    for side in (0, 1):
+        for m in range(NG):
+            jg = NG - 1 - m if side == 0 else NG + n[1] + m          # ghost row (padded index)
+            ji = NG + m if side == 0 else NG + n[1] - 1 - m           # the interior row it mirrors
+            ri, Ui, pi, Ti = prim(q[:, NG:-NG, ji, NG:-NG])
+            rg, Ug, pg, Tg = prim(q[:, NG:-NG, jg, NG:-NG])
+            assert np.abs(rg - ri).min() > 1e-3                       # the densities really differ
+            np.testing.assert_allclose(0.5 * (Ug + Ui), 0.0, atol=1e-14)
+            np.testing.assert_allclose(0.5 * (Tg + Ti), Tw, rtol=1e-13)
+            np.testing.assert_allclose(pg, pi, rtol=1e-13)
+
+
 def test_tangential_values_non_oscillatory_at_a_step(oracle):
     """R-T: the Gauss-point values of the tangential reconstruction come from
     WENO-Z, so next to a density step across the tangential direction they
