@@ -4,11 +4,14 @@
 // is rounded to nearest exactly as the scalar instruction would round it, so
 // error-free transformations (TwoSum) stay exact lane by lane.
 //
-// The mixed-precision flux pass reduces its staged first-tangential rows
-// two row types at a time with these: WENO-Z to the two Gauss abscissae, the
-// quartic point values and derivatives, and the float-float additions that
-// rebuild a value from its stencil centre (the same formulas as the scalar
-// templates of hgks_device.cuh and hgks_ff.cuh, written out per lane pair).
+// The mixed-precision passes use them for their reconstructions: the normal
+// pass runs the left and right stencils of a component as one pair (WENO-Z
+// to the cell edges), the first tangential pass reduces its rows two at a
+// time, and the flux pass reduces the two row types of each staging step
+// together (WENO-Z to the two Gauss abscissae, the quartic point values and
+// derivatives, and the float-float additions that rebuild a value from its
+// stencil centre).  The formulas are those of the scalar templates of
+// hgks_device.cuh and hgks_ff.cuh, written out per lane pair.
 #pragma once
 #include <cuda_runtime.h>
 
