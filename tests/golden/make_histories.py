@@ -16,6 +16,9 @@ Cases (parameters restate the workloads; R = 1, gamma = 1.4):
            (seed 2800), 200 steps at CFL 0.5.
   tgv256   The Taylor-Green vortex above at 256^3 cells, 2 steps at CFL 0.5
            (the full-size workload; about half an hour per step on 8 cores).
+  tgv32long  The Taylor-Green vortex above at 32^3 cells, 1200 steps at CFL
+           0.5 (t ~ 10.6 convective times: through the transition, where the
+           flow is chaotic and rounding differences grow).
 
 Usage: python tests/golden/make_histories.py tgv64 [channel tgv256 ...]
 """
@@ -58,6 +61,7 @@ CASES = {
     "tgv64": tgv_case(64, 200, (10, 100, 200)),
     "channel": channel_case((32, 48, 24), 200, (10, 100, 200)),
     "tgv256": tgv_case(256, 2, (1, 2)),
+    "tgv32long": tgv_case(32, 1200, (10, 100, 400, 800, 1200)),
 }
 SAMPLES = 384
 
