@@ -17,7 +17,7 @@ Cases (parameters restate the workloads; R = 1, gamma = 1.4):
   tgv256   The Taylor-Green vortex above at 256^3 cells, 2 steps at CFL 0.5
            (the full-size workload; about half an hour per step on 8 cores).
   tgv32long  The Taylor-Green vortex above at 32^3 cells, 1200 steps at CFL
-           0.5 (t ~ 10.6 convective times: through the transition, where the
+           0.5 (t ~ 11 convective times: through the transition, where the
            flow is chaotic and rounding differences grow).
 
 Usage: python tests/golden/make_histories.py tgv64 [channel tgv256 ...]
