@@ -52,10 +52,11 @@ METRIC = "cell-updates/s TGV 256^3 FP64 vs mixed at stated error; serve p50/p99 
 # so the per-face figure carries over to 256^3 (at 64^3, where the input is
 # only twice the L2, a launch moved 1.02 instead of 1.73 kB per face).
 K_FLUX_DRAM_BYTES_PER_FACE = (3341.87e6 + 306.34e6) / 2113536
-K_FLUX_TRAFFIC_CURRENT = True
+K_FLUX_TRAFFIC_CURRENT = False
 # the same for k_flux_mx (2010 MB read + 170 MB written per 128^3 launch,
 # mean of 24 launches of the current build)
 K_FLUX_MX_DRAM_BYTES_PER_FACE = (2010.1e6 + 170.2e6) / 2113536
+K_FLUX_MX_TRAFFIC_CURRENT = False
 # GB300 FP32 (non-tensor) peak: 152 SMs x 128 FP32 lanes x 2 flops per FMA x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # Table 3 of the paper: 256^3 TGV, FP64, Tesla V100, 11.697 h for 20 t_c at dt = 8.925e-4
@@ -446,7 +447,7 @@ def run_ours(args, rank, world, local_rank):
         fl_flops = model["flux_per_face"] * (n + 1) * n * n
         ach = fl_flops / (fl_ms * 1e-3) / 1e12
         mixed["roofline"] = {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                             "frac": ach / FP32_PEAK_TFLOPS, "traffic": K_FLUX_MX_DRAM_BYTES_PER_FACE * (n + 1) * n * n,
+                             "frac": ach / FP32_PEAK_TFLOPS, "traffic": K_FLUX_MX_DRAM_BYTES_PER_FACE * (n + 1) * n * n if K_FLUX_MX_TRAFFIC_CURRENT else None,
                              "traffic_note": "ncu DRAM bytes per k_flux_mx launch on TGV 128^3 scaled by faces",
                              "kernel": "k_flux_mx",
                              "peak_note": "FP32 FMA peak from unit counts and clock: 152 SMs x 128 lanes x 2 "

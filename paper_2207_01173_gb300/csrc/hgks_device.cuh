@@ -42,6 +42,19 @@ __device__ __forceinline__ float weno_recip<float>(float x)
 }
 #endif
 
+// a * b + c rounded once.  Written out where a sum has two products, because
+// there the compiler may fuse either one, and its choice can differ between
+// kernels that inline the same code (so the batch kernels would not repeat
+// the single-problem kernels bit for bit).  The counting type of the flop
+// model takes the generic form (one multiply, one add).
+template <typename T>
+__host__ __device__ __forceinline__ T fmad(T a, T b, T c)
+{
+    return a * b + c;
+}
+__host__ __device__ __forceinline__ double fmad(double a, double b, double c) { return fma(a, b, c); }
+__host__ __device__ __forceinline__ float fmad(float a, float b, float c) { return fmaf(a, b, c); }
+
 namespace hgks {
 
 constexpr int NG = 3;            // ghost layers (fifth-order WENO needs three)
@@ -456,42 +469,89 @@ struct HalfDelta {
 template <typename T, typename S>
 HGKS_HD void half_delta(const HalfSide<T> &h, const T dQ[5], S gm1, S K, HalfDelta<T> &d)
 {
-    const T dU = (dQ[1] - h.U[0] * dQ[0]) * h.ir;
-    const T dV = (dQ[2] - h.U[1] * dQ[0]) * h.ir;
-    const T dW = (dQ[3] - h.U[2] * dQ[0]) * h.ir;
-    const T dp = T(gm1) * (dQ[4] - (h.U[0] * dQ[1] + h.U[1] * dQ[2] + h.U[2] * dQ[3]) + T(0.5) * h.uu * dQ[0]);
-    const T dT = (dp - h.Tm * dQ[0]) * h.ir;
+    const T dU = fmad(-h.U[0], dQ[0], dQ[1]) * h.ir;
+    const T dV = fmad(-h.U[1], dQ[0], dQ[2]) * h.ir;
+    const T dW = fmad(-h.U[2], dQ[0], dQ[3]) * h.ir;
+    const T Ud = fmad(h.U[2], dQ[3], fmad(h.U[1], dQ[2], h.U[0] * dQ[1]));
+    const T dp = T(gm1) * fmad(T(0.5) * h.uu, dQ[0], dQ[4] - Ud);
+    const T dT = fmad(-h.Tm, dQ[0], dp) * h.ir;
     d.rho = dQ[0];
 #pragma unroll
-    for (int n = 0; n < 5; n++) d.du[n] = h.uU[n] * dU + h.uT[n] * dT;
+    for (int n = 0; n < 5; n++) d.du[n] = fmad(h.uU[n], dU, h.uT[n] * dT);
+    // <v^0> = 1 and <v^1> = V exactly: their changes are 0 and dV (index 0 is
+    // never read, see half_dphi)
+    d.dv[0] = T(0.0);
+    d.dw[0] = T(0.0);
+    d.dv[1] = dV;
+    d.dw[1] = dW;
 #pragma unroll
-    for (int n = 0; n < 4; n++) {
-        d.dv[n] = h.vV[n] * dV + h.vT[n] * dT;
-        d.dw[n] = h.wW[n] * dW + h.wT[n] * dT;
+    for (int n = 2; n < 4; n++) {
+        d.dv[n] = fmad(h.vV[n], dV, h.vT[n] * dT);
+        d.dw[n] = fmad(h.wW[n], dW, h.wT[n] * dT);
     }
     d.dxi1 = T(K) * dT;
+}
+
+// tangential factor X = <v^j><w^l> of a monomial and its change dX; the exact
+// <v^0> = <w^0> = 1 (change 0) is taken out at compile time, so X = 1 (j = l = 0)
+// never reaches here
+template <int j, int l, typename T>
+HGKS_HD void vw_factor(const HalfSide<T> &h, const HalfDelta<T> &d, T &X, T &dX)
+{
+    static_assert(j > 0 || l > 0, "X = 1 is handled by the caller");
+    if constexpr (j == 0) {
+        X = h.w[l];
+        dX = d.dw[l];
+    } else if constexpr (l == 0) {
+        X = h.v[j];
+        dX = d.dv[j];
+    } else {
+        X = h.v[j] * h.w[l];
+        dX = fmad(d.dv[j], h.w[l], h.v[j] * d.dw[l]);
+    }
+}
+
+// D(rho a X) = (drho a + rho da) X + (rho a) dX = al X + be dX for a = <u^k>_sigma
+template <int j, int l, typename T>
+HGKS_HD T dphi_term(const HalfSide<T> &h, const HalfDelta<T> &d, T al, T be)
+{
+    if constexpr (j == 0 && l == 0) {
+        return al;
+    } else {
+        T X, dX;
+        vw_factor<j, l>(h, d, X, dX);
+        return fmad(al, X, be * dX);
+    }
 }
 
 // directional derivative of Phi_m along the change d (product rule)
 template <int E, int J, int L, typename T>
 HGKS_HD void half_dphi(const HalfSide<T> &h, const HalfDelta<T> &d, T o[5])
 {
-    // D(rho a b c) = drho abc + rho (da bc + a (db c + b dc))
-    auto prod = [&](const T &a, const T &da, const T &b, const T &db, const T &c, const T &dc, T &val) -> T {
-        const T bc = b * c, dbc = db * c + b * dc;
-        val = a * bc;
-        return d.rho * val + h.rho * (da * bc + a * dbc);
-    };
-    T v0, v1, v2, v3, v4, v5, v6;
-    o[0] = prod(h.u[E], d.du[E], h.v[J], d.dv[J], h.w[L], d.dw[L], v0);
-    o[1] = prod(h.u[E + 1], d.du[E + 1], h.v[J], d.dv[J], h.w[L], d.dw[L], v1);
-    o[2] = prod(h.u[E], d.du[E], h.v[J + 1], d.dv[J + 1], h.w[L], d.dw[L], v2);
-    o[3] = prod(h.u[E], d.du[E], h.v[J], d.dv[J], h.w[L + 1], d.dw[L + 1], v3);
-    const T p4 = prod(h.u[E + 2], d.du[E + 2], h.v[J], d.dv[J], h.w[L], d.dw[L], v4);
-    const T p5 = prod(h.u[E], d.du[E], h.v[J + 2], d.dv[J + 2], h.w[L], d.dw[L], v5);
-    const T p6 = prod(h.u[E], d.du[E], h.v[J], d.dv[J], h.w[L + 2], d.dw[L + 2], v6);
-    // xi^2 term: D(rho xi1 abc) = xi1 D(rho abc) + rho abc dxi1
-    o[4] = T(0.5) * (p4 + p5 + p6 + h.xi1 * o[0] + h.rho * v0 * d.dxi1);
+    // a = <u^(E+k)>_sigma, k = 0, 1, 2: al_k = D(rho a) and be_k = rho a
+    T al[3], be[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        al[k] = fmad(d.rho, h.u[E + k], h.rho * d.du[E + k]);
+        be[k] = h.rho * h.u[E + k];
+    }
+    o[0] = dphi_term<J, L>(h, d, al[0], be[0]);
+    o[1] = dphi_term<J, L>(h, d, al[1], be[1]);
+    o[2] = dphi_term<J + 1, L>(h, d, al[0], be[0]);
+    o[3] = dphi_term<J, L + 1>(h, d, al[0], be[0]);
+    const T p4 = dphi_term<J, L>(h, d, al[2], be[2]);
+    const T p5 = dphi_term<J + 2, L>(h, d, al[0], be[0]);
+    const T p6 = dphi_term<J, L + 2>(h, d, al[0], be[0]);
+    // xi^2 term: D(rho <xi^2> a X) = <xi^2> D(rho a X) + (rho a X) d<xi^2>
+    T v0;
+    if constexpr (J == 0 && L == 0) {
+        v0 = be[0];
+    } else {
+        T X, dX;
+        vw_factor<J, L>(h, d, X, dX);
+        v0 = be[0] * X;
+    }
+    o[4] = T(0.5) * fmad(v0, d.dxi1, fmad(h.xi1, o[0], p4 + p5 + p6));
 }
 
 // time change of the conserved variables of an Euler state: d_t Q = -sum_d DF_d(Q)[d_d Q]
