@@ -46,17 +46,17 @@ MA, RE, PR, OMEGA, CFL = 0.1, 1600.0, 0.72, 0.7, 0.5
 METRIC = "cell-updates/s TGV 256^3 FP64 vs mixed at stated error; serve p50/p99 ms"
 # DRAM bytes per face of one k_flux launch (dram__bytes_read.sum +
 # dram__bytes_write.sum, mean of the 30 k_flux launches of an ncu capture of
-# `bench.py --n 128 --steps 1 --warmup 3` on the current build: 3342 MB read +
-# 306 MB written for 2,113,536 faces), scaled by the faces of a launch.  The
+# `bench.py --n 128 --steps 1 --warmup 3` on the current build: 3219 MB read +
+# 244 MB written for 2,113,536 faces), scaled by the faces of a launch.  The
 # 128^3 input of the pass (1.9 GB of first-tangential records) is 15x the L2,
 # so the per-face figure carries over to 256^3 (at 64^3, where the input is
 # only twice the L2, a launch moved 1.02 instead of 1.73 kB per face).
-K_FLUX_DRAM_BYTES_PER_FACE = (3341.87e6 + 306.34e6) / 2113536
-K_FLUX_TRAFFIC_CURRENT = False
+K_FLUX_DRAM_BYTES_PER_FACE = (3219.49e6 + 243.97e6) / 2113536
+K_FLUX_TRAFFIC_CURRENT = True
 # the same for k_flux_mx (2010 MB read + 170 MB written per 128^3 launch,
 # mean of 24 launches of the current build)
-K_FLUX_MX_DRAM_BYTES_PER_FACE = (2010.1e6 + 170.2e6) / 2113536
-K_FLUX_MX_TRAFFIC_CURRENT = False
+K_FLUX_MX_DRAM_BYTES_PER_FACE = (2009.60e6 + 170.24e6) / 2113536
+K_FLUX_MX_TRAFFIC_CURRENT = True
 # GB300 FP32 (non-tensor) peak: 152 SMs x 128 FP32 lanes x 2 flops per FMA x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # Table 3 of the paper: 256^3 TGV, FP64, Tesla V100, 11.697 h for 20 t_c at dt = 8.925e-4

@@ -293,7 +293,7 @@ HGKS_HD T viscosity(const Params &P, T Tm)
 // primitive and derived quantities of one Maxwellian (R = 1)
 template <typename T>
 struct Gas {
-    T rho, ir, U[3], uu, p, Tm, tl, lam, E;  // tl = 2 lambda = 1/T, E = rho E
+    T rho, ir, U[3], uu, p, Tm, E;  // Tm = p / rho, E = rho E
 };
 
 template <typename T, typename S>
@@ -309,8 +309,6 @@ HGKS_HD Gas<T> gas_of(const T Q[5], S gm1)
     g.E = Q[4];
     g.p = T(gm1) * (Q[4] - T(0.5) * Q[0] * g.uu);
     g.Tm = g.p * g.ir;
-    g.tl = T(1.0) / g.Tm;
-    g.lam = T(0.5) * g.tl;
     return g;
 }
 
@@ -464,18 +462,19 @@ HGKS_HD void half_phi(const HalfSide<T> &h, T o[5])
 template <typename T>
 struct HalfDelta {
     T rho, du[5], dv[4], dw[4], dxi1;
+    T dP[4];  // changes of U, V, W and T (rho: above)
+    T dp;     // change of the pressure (set by half_delta only)
 };
 
+// the moment changes from the primitive changes (drho, dU, dV, dW, dT)
 template <typename T, typename S>
-HGKS_HD void half_delta(const HalfSide<T> &h, const T dQ[5], S gm1, S K, HalfDelta<T> &d)
+HGKS_HD void half_delta_prim(const HalfSide<T> &h, T drho, T dU, T dV, T dW, T dT, S K, HalfDelta<T> &d)
 {
-    const T dU = fmad(-h.U[0], dQ[0], dQ[1]) * h.ir;
-    const T dV = fmad(-h.U[1], dQ[0], dQ[2]) * h.ir;
-    const T dW = fmad(-h.U[2], dQ[0], dQ[3]) * h.ir;
-    const T Ud = fmad(h.U[2], dQ[3], fmad(h.U[1], dQ[2], h.U[0] * dQ[1]));
-    const T dp = T(gm1) * fmad(T(0.5) * h.uu, dQ[0], dQ[4] - Ud);
-    const T dT = fmad(-h.Tm, dQ[0], dp) * h.ir;
-    d.rho = dQ[0];
+    d.rho = drho;
+    d.dP[0] = dU;
+    d.dP[1] = dV;
+    d.dP[2] = dW;
+    d.dP[3] = dT;
 #pragma unroll
     for (int n = 0; n < 5; n++) d.du[n] = fmad(h.uU[n], dU, h.uT[n] * dT);
     // <v^0> = 1 and <v^1> = V exactly: their changes are 0 and dV (index 0 is
@@ -490,6 +489,56 @@ HGKS_HD void half_delta(const HalfSide<T> &h, const T dQ[5], S gm1, S K, HalfDel
         d.dw[n] = fmad(h.wW[n], dW, h.wT[n] * dT);
     }
     d.dxi1 = T(K) * dT;
+}
+
+template <typename T, typename S>
+HGKS_HD void half_delta(const HalfSide<T> &h, const T dQ[5], S gm1, S K, HalfDelta<T> &d)
+{
+    const T dU = fmad(-h.U[0], dQ[0], dQ[1]) * h.ir;
+    const T dV = fmad(-h.U[1], dQ[0], dQ[2]) * h.ir;
+    const T dW = fmad(-h.U[2], dQ[0], dQ[3]) * h.ir;
+    const T Ud = fmad(h.U[2], dQ[3], fmad(h.U[1], dQ[2], h.U[0] * dQ[1]));
+    const T dp = T(gm1) * fmad(T(0.5) * h.uu, dQ[0], dQ[4] - Ud);
+    const T dT = fmad(-h.Tm, dQ[0], dp) * h.ir;
+    half_delta_prim(h, dQ[0], dU, dV, dW, dT, K, d);
+    d.dp = dp;
+}
+
+// Minus the time change of a side's primitives, summed over the three
+// directions from their primitive changes.  The Euler equations in primitive
+// form (R = 1, p = rho T) give
+//   d_t rho = -(U.grad rho + rho div U),   d_t U_k = -(U.grad U_k + d_k p / rho),
+//   d_t T = -(U.grad T + (gamma - 1) T div U),
+// the linear map d_t Q = -sum_d DF_d(Q)[d_d Q] (the Euler-flux Jacobians)
+// written in primitives.  Direction D adds its terms; D = 0 starts the sums.
+template <typename T>
+struct HalfRate {
+    T rho, U[3], Tm;
+};
+
+template <int D, typename T, typename S>
+HGKS_HD void half_rate_add(const HalfSide<T> &h, const HalfDelta<T> &d, S gm1, HalfRate<T> &r)
+{
+    const T Ud = h.U[D], div = d.dP[D];  // U_D and d_D U_D
+    const T gT = T(gm1) * h.Tm;
+    if constexpr (D == 0) {
+        r.rho = fmad(Ud, d.rho, h.rho * div);
+#pragma unroll
+        for (int k = 0; k < 3; k++) r.U[k] = k == D ? fmad(Ud, d.dP[k], h.ir * d.dp) : Ud * d.dP[k];
+        r.Tm = fmad(Ud, d.dP[3], gT * div);
+    } else {
+        r.rho = fmad(Ud, d.rho, fmad(h.rho, div, r.rho));
+#pragma unroll
+        for (int k = 0; k < 3; k++) r.U[k] = fmad(Ud, d.dP[k], k == D ? fmad(h.ir, d.dp, r.U[k]) : r.U[k]);
+        r.Tm = fmad(Ud, d.dP[3], fmad(gT, div, r.Tm));
+    }
+}
+
+// the side's moment changes along its time slope
+template <typename T, typename S>
+HGKS_HD void half_delta_time(const HalfSide<T> &h, const HalfRate<T> &r, S K, HalfDelta<T> &d)
+{
+    half_delta_prim(h, -r.rho, -r.U[0], -r.U[1], -r.U[2], -r.Tm, K, d);
 }
 
 // tangential factor X = <v^j><w^l> of a monomial and its change dX; the exact
@@ -554,20 +603,6 @@ HGKS_HD void half_dphi(const HalfSide<T> &h, const HalfDelta<T> &d, T o[5])
     o[4] = T(0.5) * fmad(v0, d.dxi1, fmad(h.xi1, o[0], p4 + p5 + p6));
 }
 
-// time change of the conserved variables of an Euler state: d_t Q = -sum_d DF_d(Q)[d_d Q]
-template <typename T, typename S>
-HGKS_HD void euler_dtq(const Gas<T> &g, const T dq[3][5], S gm1, T o[5])
-{
-    T s[5];
-    euler_dflux<0>(g, dq[0], gm1, o);
-    euler_dflux<1>(g, dq[1], gm1, s);
-#pragma unroll
-    for (int c = 0; c < 5; c++) o[c] += s[c];
-    euler_dflux<2>(g, dq[2], gm1, s);
-#pragma unroll
-    for (int c = 0; c < 5; c++) o[c] = -(o[c] + s[c]);
-}
-
 // all half-range terms of one side: Q0 part and B4 (values), W5, B5 (slopes),
 // W6, B6 (time slope), summed over the three derivative directions
 template <typename T, typename S>
@@ -579,10 +614,12 @@ HGKS_HD void half_terms(const T Q[5], const T dq[3][5], S gm1, S K, bool pos, T 
     half_phi<0, 0, 0>(h, q0);
     half_phi<1, 0, 0>(h, b4);
     HalfDelta<T> dd;
+    HalfRate<T> rt;
     T s[5];
     half_delta(h, dq[0], gm1, K, dd);  // normal direction: m = u (W5), u^2 (B5)
     half_dphi<1, 0, 0>(h, dd, w5);
     half_dphi<2, 0, 0>(h, dd, b5);
+    half_rate_add<0>(h, dd, gm1, rt);
     half_delta(h, dq[1], gm1, K, dd);  // first tangential: m = v, u v
     half_dphi<0, 1, 0>(h, dd, s);
 #pragma unroll
@@ -590,6 +627,7 @@ HGKS_HD void half_terms(const T Q[5], const T dq[3][5], S gm1, S K, bool pos, T 
     half_dphi<1, 1, 0>(h, dd, s);
 #pragma unroll
     for (int c = 0; c < 5; c++) b5[c] += s[c];
+    half_rate_add<1>(h, dd, gm1, rt);
     half_delta(h, dq[2], gm1, K, dd);  // second tangential: m = w, u w
     half_dphi<0, 0, 1>(h, dd, s);
 #pragma unroll
@@ -597,20 +635,9 @@ HGKS_HD void half_terms(const T Q[5], const T dq[3][5], S gm1, S K, bool pos, T 
     half_dphi<1, 0, 1>(h, dd, s);
 #pragma unroll
     for (int c = 0; c < 5; c++) b5[c] += s[c];
+    half_rate_add<2>(h, dd, gm1, rt);
     // time slope of the side's Maxwellian
-    Gas<T> g;
-    g.rho = h.rho;
-    g.ir = h.ir;
-    g.U[0] = h.U[0];
-    g.U[1] = h.U[1];
-    g.U[2] = h.U[2];
-    g.uu = h.uu;
-    g.E = h.E;
-    g.p = h.p;
-    g.Tm = h.Tm;
-    T dtq[5];
-    euler_dtq(g, dq, gm1, dtq);
-    half_delta(h, dtq, gm1, K, dd);
+    half_delta_time(h, rt, K, dd);
     half_dphi<0, 0, 0>(h, dd, w6);
     half_dphi<1, 0, 0>(h, dd, b6);
 }
@@ -625,7 +652,6 @@ __host__ __device__ __noinline__ void gks_point_flux(const T Ql[5], const T Qr[5
                                                           T Fn[5], T dFn[5])
 {
     const double gm1 = P.gamma - 1.0, K = P.K;
-    const Gas<T> gl = gas_of(Ql, gm1), gr = gas_of(Qr, gm1);
     // half-range terms of the two sides (values and directional derivatives)
     T ql[5], b4l[5], w5l[5], b5l[5], w6l[5], b6l[5], qr[5], b4r[5], w5r[5], b5r[5], w6r[5], b6r[5];
     half_terms(Ql, dl, gm1, K, true, ql, b4l, w5l, b5l, w6l, b6l);

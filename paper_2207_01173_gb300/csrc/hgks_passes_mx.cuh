@@ -140,11 +140,13 @@ static __host__ __device__ __forceinline__ void side_terms_mx(const float q[5], 
     HalfSide<float> h;
     half_side_setup(q, gm1, K, POS, h);
     HalfDelta<float> dd;
+    HalfRate<float> rt;
     float s[5];
     half_phi<1, 0, 0>(h, b4);
     half_delta(h, dq[0], gm1, K, dd);
     half_dphi<1, 0, 0>(h, dd, w5);
     half_dphi<2, 0, 0>(h, dd, b5);
+    half_rate_add<0>(h, dd, gm1, rt);
     half_delta(h, dq[1], gm1, K, dd);
     half_dphi<0, 1, 0>(h, dd, s);
 #pragma unroll
@@ -152,6 +154,7 @@ static __host__ __device__ __forceinline__ void side_terms_mx(const float q[5], 
     half_dphi<1, 1, 0>(h, dd, s);
 #pragma unroll
     for (int c = 0; c < 5; c++) b5[c] += s[c];
+    half_rate_add<1>(h, dd, gm1, rt);
     half_delta(h, dq[2], gm1, K, dd);
     half_dphi<0, 0, 1>(h, dd, s);
 #pragma unroll
@@ -159,11 +162,9 @@ static __host__ __device__ __forceinline__ void side_terms_mx(const float q[5], 
     half_dphi<1, 0, 1>(h, dd, s);
 #pragma unroll
     for (int c = 0; c < 5; c++) b5[c] += s[c];
+    half_rate_add<2>(h, dd, gm1, rt);
     // time slope of the side
-    const Gas<float> g = gas_of(q, gm1);
-    float tq[5];
-    euler_dtq(g, dq, gm1, tq);
-    half_delta(h, tq, gm1, K, dd);
+    half_delta_time(h, rt, K, dd);
     half_dphi<0, 0, 0>(h, dd, w6);
     half_dphi<1, 0, 0>(h, dd, b6);
     if (small_jump) {

@@ -91,7 +91,7 @@ def test_flop_model_counts_the_kernel_arithmetic():
     property of the code (they change only when the arithmetic does)."""
     from paper_2207_01173_gb300 import hgks
     m = hgks.flop_model((256, 256, 256))
-    assert m["flux_per_face"] == 14182 and m["div_per_face_flux"] == 102 and m["special_per_face_flux"] == 32
+    assert m["flux_per_face"] == 13342 and m["div_per_face_flux"] == 82 and m["special_per_face_flux"] == 32
     assert m["normal_per_face"] == 1068 and m["tan1_per_pos"] == 2250
     # a step: two stages x three directions of each pass plus the cell passes
     faces = 257 * 256 * 256
