@@ -33,6 +33,31 @@ void kh_point_flux(int n, const double *Ql, const double *Qr, const double *dl, 
                                      Fn + 5 * i, dFn + 5 * i);
 }
 
+// the time change of a side's primitives (rho, U, V, W, T) along its time
+// slope, as the flux forms it from the spatial changes of the three
+// directions (primitive-form Euler equations); per case Q [5], dq [3][5]
+void kh_side_time_rate(int n, const double *Q, const double *dq, double gamma, double *out)
+{
+    const double gm1 = gamma - 1.0, K = (5.0 - 3.0 * gamma) / (gamma - 1.0);
+    for (int i = 0; i < n; i++) {
+        hgks::HalfSide<double> h;
+        hgks::half_side_setup(Q + 5 * i, gm1, K, true, h);
+        hgks::HalfDelta<double> d;
+        hgks::HalfRate<double> r;
+        const double *g = dq + 15 * i;
+        hgks::half_delta(h, g, gm1, K, d);
+        hgks::half_rate_add<0>(h, d, gm1, r);
+        hgks::half_delta(h, g + 5, gm1, K, d);
+        hgks::half_rate_add<1>(h, d, gm1, r);
+        hgks::half_delta(h, g + 10, gm1, K, d);
+        hgks::half_rate_add<2>(h, d, gm1, r);
+        hgks::half_delta_time(h, r, K, d);
+        double *o = out + 5 * i;
+        o[0] = d.rho;
+        for (int k = 0; k < 4; k++) o[1 + k] = d.dP[k];
+    }
+}
+
 // per case: five averages X; outputs (left edge, right edge, value at -sqrt3/6,
 // value at +sqrt3/6) by WENO-Z and (value -, value +, slope -, slope +) of the
 // quartic, slopes in index units

@@ -44,6 +44,7 @@ def kh(tmp_path_factory):
     L.kh_point_flux.argtypes = [C.c_int, dp, dp, dp, dp, dp, C.c_double, C.c_double, C.c_int, C.c_double,
                                 C.c_double, C.c_double, C.c_double, dp, dp]
     L.kh_reconstruct.argtypes = [C.c_int, dp, dp, dp]
+    L.kh_side_time_rate.argtypes = [C.c_int, dp, dp, C.c_double, dp]
     fp = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
     L.kh_point_flux_mixed.argtypes = [C.c_int] + [fp] * 7 + [C.c_double, C.c_double, C.c_int, C.c_double,
                                                               C.c_double, C.c_double, C.c_double, dp, dp, C.c_int]
@@ -93,6 +94,48 @@ def test_point_flux_matches_oracle(oracle, kh, jump, visc):
         scale = max(np.abs(F_ref).max(), 1.0)
         np.testing.assert_allclose(Fn[i], F_ref, rtol=0, atol=1e-13 * scale)
         np.testing.assert_allclose(dFn[i], dF_ref, rtol=0, atol=1e-13 * max(np.abs(dF_ref).max(), scale / dt))
+
+
+def _euler_flux(Q, d):
+    """Euler flux along direction d of conservative states Q [..., 5]; plain
+    arithmetic only, so it also takes complex arguments."""
+    rho, m, E = Q[..., 0], Q[..., 1:4], Q[..., 4]
+    u = m / rho[..., None]
+    p = (GAMMA - 1.0) * (E - 0.5 * (m * u).sum(-1))
+    F = np.empty_like(Q)
+    F[..., 0] = m[..., d]
+    F[..., 1:4] = m[..., d, None] * u
+    F[..., 1 + d] += p
+    F[..., 4] = u[..., d] * (E + p)
+    return F
+
+
+def _primitives(Q):
+    rho = Q[..., 0]
+    u = Q[..., 1:4] / rho[..., None]
+    p = (GAMMA - 1.0) * (Q[..., 4] - 0.5 * rho * (u * u).sum(-1))
+    return np.concatenate([rho[..., None], u, (p / rho)[..., None]], -1)
+
+
+def test_side_time_slope_is_the_euler_time_derivative(kh):
+    """A side's time slope enters the flux through the time change of its
+    primitives (rho, U, V, W, T), which the kernels sum from the Euler
+    equations in primitive form.  Reference: the conservative form
+    d_t Q = -sum_d dF_d/dQ . d_d Q, differentiated by the complex step (exact
+    to rounding) and taken to primitives the same way."""
+    rng = np.random.default_rng(2207)
+    n = 500
+    Q, _ = _states(rng, n, 0.0)
+    dq = rng.normal(size=(n, 3, 5)) * np.abs(Q)[:, None, :]
+    out = np.zeros((n, 5))
+    kh.kh_side_time_rate(n, Q, np.ascontiguousarray(dq.reshape(n, 15)), GAMMA, out)
+    h = 1e-30
+    dtq = -sum(_euler_flux(Q + 1j * h * dq[:, d], d).imag / h for d in range(3))
+    ref = _primitives(Q + 1j * h * dtq).imag / h
+    # per-case scale: the size of the terms that the Euler equations sum
+    scale = np.abs(dq).sum(axis=(1, 2))[:, None] * (1.0 + np.abs(Q).max(axis=1))[:, None]
+    assert np.max(np.abs(out - ref) / scale) < 1e-14
+    assert np.max(np.abs(ref) / scale) > 1e-3  # the comparison is not of vanishing quantities
 
 
 @pytest.mark.parametrize("kind", ["smooth", "rough", "step"])
