@@ -14,7 +14,9 @@
 //   * the micro-slope terms of the flux (a g = dg/dQ . dQ for a Maxwellian)
 //     as directional derivatives of moment functions: Euler-flux Jacobians for
 //     the full-range equilibrium terms, differentiated half-range moments for
-//     the l/r terms, so no 5x5 slope system is ever solved.
+//     the l/r terms, so no 5x5 slope system is ever solved; the time slope of
+//     each l/r side enters through its primitives' time changes, taken from
+//     the Euler equations in primitive form.
 // The arithmetic routines are templates on the scalar type T (double on the
 // device; a host operation-counting type instantiates the same code to count
 // the scheme's floating-point work).
