@@ -57,6 +57,10 @@ K_FLUX_TRAFFIC_CURRENT = True
 # mean of 24 launches of the current build)
 K_FLUX_MX_DRAM_BYTES_PER_FACE = (2009.60e6 + 170.24e6) / 2113536
 K_FLUX_MX_TRAFFIC_CURRENT = True
+# executed FP64 flops per k_flux face (2 DFMA + DMUL + DADD thread
+# instructions from sass__thread_inst_executed_true_per_opcode, ncu capture of
+# `bench.py --n 48` on the current build), for the roofline's note
+K_FLUX_EXECUTED_FP64_FLOPS_PER_FACE = 14345
 # GB300 FP32 (non-tensor) peak: 152 SMs x 128 FP32 lanes x 2 flops per FMA x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # Table 3 of the paper: 256^3 TGV, FP64, Tesla V100, 11.697 h for 20 t_c at dt = 8.925e-4
@@ -534,7 +538,13 @@ def run_ours(args, rank, world, local_rank):
                                   % fp64_peak,
                      "algorithmic_flops_per_launch": flops_per_launch,
                      "flops_per_face": model["flux_per_face"], "faces_per_launch": faces_per_launch,
-                     "avg_launch_ms": flux_ms / flux_launches},
+                     "avg_launch_ms": flux_ms / flux_launches,
+                     "executed_frac": K_FLUX_EXECUTED_FP64_FLOPS_PER_FACE * faces_per_launch
+                                      / (flux_ms / flux_launches * 1e-3) / 1e12 / peak,
+                     "flops_note": "hgks_flop_model counts the written arithmetic of the current flux; "
+                                   "divisions and special functions count 1 each, so ncu's executed FP64 "
+                                   "flops per face (%d at 48^3) are above the count and frac sits below "
+                                   "the FP64 pipe's 87 %% utilisation" % K_FLUX_EXECUTED_FP64_FLOPS_PER_FACE},
         "step_flops": model["per_step"],
         "step_tflops": model["per_step"] / (ms_per_step * 1e-3) / 1e12,
         "kernel_ms_per_step": kernel_ms,
